@@ -1,0 +1,685 @@
+/*
+ * zoomy_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, FP64 CPU implementation of the explicit finite-volume step of
+ * the shallow-water / shallow-moment hierarchy (Eq. (sme), Sec. 1; the 2D SME
+ * system and friction closure of Sec. 3.4; the hyperbolic predictor
+ * Eq. (PDE-hyperbolic) and the source split Eq. (PDE-source), Sec. 2.1.2).
+ *
+ * It exists to check the GPU library.  Only the tests, __graft_entry__.smoke()
+ * and bench.py's cpu_baseline / reference leg may load it.  It shares no code,
+ * header, table or constant with the CUDA path: the basis integrals are
+ * computed here from the Legendre recurrence and Gauss-Legendre quadrature,
+ * the mesh geometry and neighbours are rebuilt here from the raw mesh
+ * description, and every model term is written out from its definition with
+ * plain loops, cell by cell, each face evaluated from the side of the cell
+ * being updated.  Compile with -ffp-contract=off.
+ *
+ * Readings of points where the paper is silent or inconsistent (all listed in
+ * the design notes of the repository):
+ *   R1 basis       phi_k(z) = P_k(1-2z): shifted Legendre, phi_k(0) = 1, z = 0 at the bed.
+ *   R2 NC matrix   rows and columns k,l >= 1 only; row hA_k, column hA_l (x):
+ *                  -u_m delta_kl + sum_{j>=1} alpha_j B_kjl / M_k with
+ *                  B_kjl = <phi_k', phi_j Phi_l> (index order of Eq. (sme));
+ *                  y-direction columns hB_l carry the same entries.
+ *   R3 wave speed  s = |u_mean| + sqrt(g h + sum_{k>=1}|a_k|^2) + sum_{k>=2}|a_k|.
+ *   R4 friction    slip  S_k = -(2k+1) (C/rho) u_b,  u_b = sum_k alpha_k (phi_k(0) = 1), k = 0..N;
+ *                  Newtonian S_k = -(2k+1) (nu/(rho h)) sum_i C_ik alpha_i, C_ik = <phi_i', phi_k'>;
+ *                  Manning bottom stress g n^2 |u_b| u_b / h^(1/3) in place of (C/rho) u_b.
+ *   R5 time        SSP-RK2; per stage Y = X + dt L(X) with L = hyperbolic part + Newtonian
+ *                  source at X; then the bottom stress as a linearly implicit cell-local
+ *                  update (coefficient frozen at Y), then the dry cut.
+ *   R6 scheme      path-conservative Rusanov with hydrostatic reconstruction: per face
+ *                  |e| [ 1/2(F_n(Qi*)+F_n(Qj*)) - 1/2 s_f (Qj*-Qi*) - P(hi*) n
+ *                        + 1/2 Btilde_n (Qj*-Qi*) ],  Btilde from 3-point Gauss-Legendre
+ *                  along the straight segment in conserved variables.
+ *   R7 CFL         dt = CFL * min_i Delta_i / max_i s_i,  Delta_i = 2|Omega_i|/P_i.
+ *   R8 dry cells   velocities are zero where h <= h_dry (also along the NC path).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_MAXN 8
+#define OR_MAXM (OR_MAXN + 1)
+#define OR_MAXV (1 + 2 * OR_MAXM)
+#define OR_NQ 16 /* Gauss-Legendre points for the basis integrals (exact to degree 31) */
+
+/* ------------------------------------------------------------------------- */
+/* Legendre polynomials and the shifted basis (reading R1)                    */
+/* ------------------------------------------------------------------------- */
+
+/* P_0..P_n and their derivatives at x by the three-term recurrence
+ * (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1},   P'_{k+1} = P'_{k-1} + (2k+1) P_k. */
+static void legendre_all(int n, double x, double *P, double *dP)
+{
+    P[0] = 1.0;
+    dP[0] = 0.0;
+    if (n >= 1) {
+        P[1] = x;
+        dP[1] = 1.0;
+    }
+    for (int k = 1; k < n; ++k) {
+        P[k + 1] = ((2.0 * k + 1.0) * x * P[k] - k * P[k - 1]) / (k + 1.0);
+        dP[k + 1] = dP[k - 1] + (2.0 * k + 1.0) * P[k];
+    }
+}
+
+/* phi_k(z) = P_k(1-2z), phi_k'(z) = -2 P_k'(1-2z),
+ * Phi_k(z) = int_0^z phi_k = z for k = 0, and for k >= 1, from
+ * int P_k dx = (P_{k+1} - P_{k-1})/(2k+1) and dx = -2 dz:
+ * Phi_k(z) = -(P_{k+1}(1-2z) - P_{k-1}(1-2z)) / (2(2k+1)). */
+static void basis_eval(int N, double z, double *phi, double *dphi, double *Phi)
+{
+    double P[OR_MAXN + 3], dP[OR_MAXN + 3];
+    double x = 1.0 - 2.0 * z;
+    legendre_all(N + 1, x, P, dP);
+    for (int k = 0; k <= N; ++k) {
+        phi[k] = P[k];
+        dphi[k] = -2.0 * dP[k];
+        if (k == 0)
+            Phi[k] = z;
+        else
+            Phi[k] = -(P[k + 1] - P[k - 1]) / (2.0 * (2.0 * k + 1.0));
+    }
+}
+
+/* n-point Gauss-Legendre rule on [0,1] (Newton iteration on P_n). */
+static void gauss_legendre01(int n, double *z, double *w)
+{
+    for (int i = 0; i < n; ++i) {
+        double x = cos(M_PI * (i + 0.75) / (n + 0.5));
+        double P[64], dP[64];
+        for (int it = 0; it < 100; ++it) {
+            legendre_all(n, x, P, dP);
+            double dx = P[n] / dP[n];
+            x -= dx;
+            if (fabs(dx) < 1e-15) { /* converged: one more Newton step polishes the last bits */
+                legendre_all(n, x, P, dP);
+                x -= P[n] / dP[n];
+                break;
+            }
+        }
+        legendre_all(n, x, P, dP);
+        double wi = 2.0 / ((1.0 - x * x) * dP[n] * dP[n]);
+        z[i] = 0.5 * (1.0 + x);
+        w[i] = 0.5 * wi;
+    }
+}
+
+/* Basis integrals (Sec. 2.1.1 "Basismatrices", Sec. 3.4):
+ *   M[k]            = <phi_k, phi_k>
+ *   A[(i*m+j)*m+k]  = <phi_i phi_j, phi_k>
+ *   B[(k*m+j)*m+l]  = <phi_k', phi_j Phi_l>
+ *   C[i*m+k]        = <phi_i', phi_k'>
+ *   phi0[k]         = phi_k(0)
+ * with m = N+1 and <f,g> = int_0^1 f g dz. */
+int or_basis_tables(int N, double *M, double *A, double *B, double *C, double *phi0)
+{
+    if (N < 0 || N > OR_MAXN) return 1;
+    int m = N + 1;
+    double zq[OR_NQ], wq[OR_NQ];
+    gauss_legendre01(OR_NQ, zq, wq);
+    memset(M, 0, sizeof(double) * m);
+    memset(A, 0, sizeof(double) * m * m * m);
+    memset(B, 0, sizeof(double) * m * m * m);
+    memset(C, 0, sizeof(double) * m * m);
+    for (int q = 0; q < OR_NQ; ++q) {
+        double phi[OR_MAXM], dphi[OR_MAXM], Phi[OR_MAXM];
+        basis_eval(N, zq[q], phi, dphi, Phi);
+        for (int i = 0; i < m; ++i) {
+            M[i] += wq[q] * phi[i] * phi[i];
+            for (int k = 0; k < m; ++k) C[i * m + k] += wq[q] * dphi[i] * dphi[k];
+            for (int j = 0; j < m; ++j)
+                for (int k = 0; k < m; ++k) {
+                    A[(i * m + j) * m + k] += wq[q] * phi[i] * phi[j] * phi[k];
+                    B[(i * m + j) * m + k] += wq[q] * dphi[i] * phi[j] * Phi[k];
+                }
+        }
+    }
+    /* Integrals that vanish by orthogonality or parity come out of the quadrature as
+     * rounding noise of order 1e-17; every non-vanishing entry for N <= 8 exceeds 1e-6. */
+    for (int i = 0; i < m * m * m; ++i) {
+        if (fabs(A[i]) < 1e-13) A[i] = 0.0;
+        if (fabs(B[i]) < 1e-13) B[i] = 0.0;
+    }
+    for (int i = 0; i < m * m; ++i)
+        if (fabs(C[i]) < 1e-13) C[i] = 0.0;
+    double phi[OR_MAXM], dphi[OR_MAXM], Phi[OR_MAXM];
+    basis_eval(N, 0.0, phi, dphi, Phi);
+    for (int k = 0; k < m; ++k) phi0[k] = phi[k];
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Model (level N, dimension 1 or 2)                                          */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    int N, dim, nv, m;
+    double g, h_dry;
+    int fric; /* 0 none, 1 slip + Newtonian, 2 Manning */
+    double C, nu, rho, manning_n;
+    double M[OR_MAXM];
+    double A[OR_MAXM * OR_MAXM * OR_MAXM];
+    double B[OR_MAXM * OR_MAXM * OR_MAXM];
+    double Cm[OR_MAXM * OR_MAXM];
+    double phi0[OR_MAXM];
+} or_model;
+
+/* Variable order.  1D: (h, hA_0..hA_N).  2D: (h, hA_0, hB_0, hA_1..hA_N, hB_1..hB_N),
+ * where hA_k = h alpha_k (x-velocity moments) and hB_k = h beta_k (y-velocity moments). */
+static int ia(const or_model *md, int k)
+{
+    if (md->dim == 1) return 1 + k;
+    return k == 0 ? 1 : 2 + k;
+}
+static int ib(const or_model *md, int k)
+{
+    return k == 0 ? 2 : 2 + md->N + k;
+}
+
+or_model *or_model_new(int N, int dim, double g, double h_dry, int fric, double C, double nu,
+                       double rho, double manning_n)
+{
+    if (N < 0 || N > OR_MAXN || (dim != 1 && dim != 2)) return NULL;
+    or_model *md = (or_model *)calloc(1, sizeof(or_model));
+    md->N = N;
+    md->dim = dim;
+    md->m = N + 1;
+    md->nv = dim == 1 ? 1 + md->m : 1 + 2 * md->m;
+    md->g = g;
+    md->h_dry = h_dry;
+    md->fric = fric;
+    md->C = C;
+    md->nu = nu;
+    md->rho = rho;
+    md->manning_n = manning_n;
+    or_basis_tables(N, md->M, md->A, md->B, md->Cm, md->phi0);
+    return md;
+}
+void or_model_free(or_model *md) { free(md); }
+int or_model_nv(const or_model *md) { return md->nv; }
+
+/* Velocity moments alpha_k = hA_k / h, beta_k = hB_k / h; zero where h <= h_dry (R8). */
+static void velocities(const or_model *md, const double *q, double *al, double *be)
+{
+    double h = q[0];
+    for (int k = 0; k < md->m; ++k) {
+        al[k] = 0.0;
+        be[k] = 0.0;
+        if (h > md->h_dry) {
+            al[k] = q[ia(md, k)] / h;
+            if (md->dim == 2) be[k] = q[ib(md, k)] / h;
+        }
+    }
+}
+
+/* Normal flux F_n = nx F_x + ny F_y (Eq. (sme) and the 2D SME flux of Sec. 3.4):
+ *   h   row: h (alpha_0 nx + beta_0 ny)
+ *   hA_k row: nx [h sum_ij alpha_i alpha_j A_ijk / M_k + delta_k0 g h^2/2] + ny h sum_ij beta_i alpha_j A_ijk / M_k
+ *   hB_k row: nx h sum_ij alpha_i beta_j A_ijk / M_k + ny [h sum_ij beta_i beta_j A_ijk / M_k + delta_k0 g h^2/2] */
+void or_flux(const or_model *md, const double *q, double nx, double ny, double *F)
+{
+    int m = md->m;
+    double al[OR_MAXM], be[OR_MAXM];
+    velocities(md, q, al, be);
+    double h = q[0];
+    for (int v = 0; v < md->nv; ++v) F[v] = 0.0;
+    F[0] = h * al[0] * nx + (md->dim == 2 ? h * be[0] * ny : 0.0);
+    for (int k = 0; k < m; ++k) {
+        double saa = 0.0, sab = 0.0, sba = 0.0, sbb = 0.0;
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < m; ++j) {
+                double a = md->A[(i * m + j) * m + k];
+                saa += al[i] * al[j] * a;
+                sab += al[i] * be[j] * a;
+                sba += be[i] * al[j] * a;
+                sbb += be[i] * be[j] * a;
+            }
+        double p = (k == 0) ? 0.5 * md->g * h * h : 0.0;
+        F[ia(md, k)] = nx * (h * saa / md->M[k] + p);
+        if (md->dim == 2) {
+            F[ia(md, k)] += ny * (h * sba / md->M[k]);
+            F[ib(md, k)] = nx * (h * sab / md->M[k]) + ny * (h * sbb / md->M[k] + p);
+        }
+    }
+}
+
+/* Nonconservative matrix B_n = nx B_x + ny B_y, row-major nv x nv (reading R2). */
+void or_nc_matrix(const or_model *md, const double *q, double nx, double ny, double *Bn)
+{
+    int m = md->m, nv = md->nv;
+    double al[OR_MAXM], be[OR_MAXM];
+    velocities(md, q, al, be);
+    for (int v = 0; v < nv * nv; ++v) Bn[v] = 0.0;
+    for (int k = 1; k < m; ++k)
+        for (int l = 1; l < m; ++l) {
+            double ea = (k == l) ? -al[0] : 0.0; /* -u_m delta_kl */
+            double eb = (k == l) ? -be[0] : 0.0; /* -v_m delta_kl */
+            for (int j = 1; j < m; ++j) {
+                ea += al[j] * md->B[(k * m + j) * m + l] / md->M[k];
+                eb += be[j] * md->B[(k * m + j) * m + l] / md->M[k];
+            }
+            /* x-direction: columns hA_l */
+            Bn[ia(md, k) * nv + ia(md, l)] += nx * ea;
+            if (md->dim == 2) {
+                Bn[ib(md, k) * nv + ia(md, l)] += nx * eb;
+                /* y-direction: columns hB_l */
+                Bn[ia(md, k) * nv + ib(md, l)] += ny * ea;
+                Bn[ib(md, k) * nv + ib(md, l)] += ny * eb;
+            }
+        }
+}
+
+/* Cell wave-speed bound (reading R3). */
+double or_wavespeed(const or_model *md, const double *q)
+{
+    double al[OR_MAXM], be[OR_MAXM];
+    velocities(md, q, al, be);
+    double h = q[0] > 0.0 ? q[0] : 0.0;
+    double um = sqrt(al[0] * al[0] + be[0] * be[0]);
+    double s2 = 0.0, s1 = 0.0;
+    for (int k = 1; k < md->m; ++k) {
+        double ak2 = al[k] * al[k] + be[k] * be[k];
+        s2 += ak2;
+        if (k >= 2) s1 += sqrt(ak2);
+    }
+    return um + sqrt(md->g * h + s2) + s1;
+}
+
+/* Newtonian bulk friction (reading R4), explicit part of the source. */
+void or_source_newtonian(const or_model *md, const double *q, double *S)
+{
+    double al[OR_MAXM], be[OR_MAXM];
+    velocities(md, q, al, be);
+    for (int v = 0; v < md->nv; ++v) S[v] = 0.0;
+    if (md->fric != 1 || !(q[0] > md->h_dry)) return;
+    double h = q[0];
+    for (int k = 0; k < md->m; ++k) {
+        double sa = 0.0, sb = 0.0;
+        for (int i = 0; i < md->m; ++i) {
+            sa += al[i] * md->Cm[i * md->m + k];
+            sb += be[i] * md->Cm[i * md->m + k];
+        }
+        S[ia(md, k)] = -(md->nu / (md->rho * h)) * sa / md->M[k];
+        if (md->dim == 2) S[ib(md, k)] = -(md->nu / (md->rho * h)) * sb / md->M[k];
+    }
+}
+
+/* Bottom stress, linearly implicit (reading R5), then the dry cut (R8), in place.
+ * The stress on row k is -(phi_k(0)/M_k) c sum_i hA_i with c = C/(rho h) (slip) or
+ * c = g n^2 |u_b| / h^(4/3) (Manning), frozen at the input state y.  The implicit
+ * system z + dt c w (1^T z) = y, w_k = phi_k(0)/M_k, is solved by the Sherman-Morrison
+ * formula z = y - dt c w (1^T y) / (1 + dt c 1^T w). */
+void or_bottom_friction(const or_model *md, double *y, double dt)
+{
+    double h = y[0];
+    int m = md->m;
+    if (!(h > md->h_dry)) {
+        for (int v = 1; v < md->nv; ++v) y[v] = 0.0;
+        return;
+    }
+    if (md->fric == 0) return;
+    double sa = 0.0, sb = 0.0;
+    for (int k = 0; k < m; ++k) {
+        sa += md->phi0[k] * y[ia(md, k)];
+        if (md->dim == 2) sb += md->phi0[k] * y[ib(md, k)];
+    }
+    double c;
+    if (md->fric == 1) {
+        c = md->C / (md->rho * h);
+    } else {
+        double ub = sa / h, vb = sb / h;
+        double n2 = md->manning_n * md->manning_n;
+        c = md->g * n2 * sqrt(ub * ub + vb * vb) / pow(h, 4.0 / 3.0);
+    }
+    double sw = 0.0;
+    for (int k = 0; k < m; ++k) sw += md->phi0[k] / md->M[k];
+    double den = 1.0 + dt * c * sw;
+    for (int k = 0; k < m; ++k) {
+        double w = md->phi0[k] / md->M[k];
+        y[ia(md, k)] -= dt * c * w * sa / den;
+        if (md->dim == 2) y[ib(md, k)] -= dt * c * w * sb / den;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Mesh (built here from the raw description, independent of the library)    */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    int64_t nc;
+    int nf;          /* faces per cell: 2 (1D), 4 (quads), 3 (triangles) */
+    int dim;
+    double *area;    /* |Omega_i| */
+    double *delta;   /* 2 |Omega_i| / P_i */
+    int64_t *nbr;    /* [nc*nf], -1 on the boundary */
+    double *fnx, *fny, *flen; /* outward unit normal and length per (cell, face) */
+    int *fbc;        /* boundary kind per (cell, face): 0 transmissive, 1 wall */
+} or_mesh;
+
+static or_mesh *mesh_alloc(int64_t nc, int nf, int dim)
+{
+    or_mesh *me = (or_mesh *)calloc(1, sizeof(or_mesh));
+    me->nc = nc;
+    me->nf = nf;
+    me->dim = dim;
+    me->area = (double *)calloc(nc, sizeof(double));
+    me->delta = (double *)calloc(nc, sizeof(double));
+    me->nbr = (int64_t *)calloc(nc * nf, sizeof(int64_t));
+    me->fnx = (double *)calloc(nc * nf, sizeof(double));
+    me->fny = (double *)calloc(nc * nf, sizeof(double));
+    me->flen = (double *)calloc(nc * nf, sizeof(double));
+    me->fbc = (int *)calloc(nc * nf, sizeof(int));
+    return me;
+}
+
+void or_mesh_free(or_mesh *me)
+{
+    if (!me) return;
+    free(me->area);
+    free(me->delta);
+    free(me->nbr);
+    free(me->fnx);
+    free(me->fny);
+    free(me->flen);
+    free(me->fbc);
+    free(me);
+}
+
+int64_t or_mesh_ncells(const or_mesh *me) { return me->nc; }
+
+/* Uniform 1D grid on [x0,x1]; bc_left, bc_right in {0 transmissive, 1 wall}. */
+or_mesh *or_mesh_1d(int64_t nx, double x0, double x1, int bc_left, int bc_right)
+{
+    or_mesh *me = mesh_alloc(nx, 2, 1);
+    double dx = (x1 - x0) / (double)nx;
+    for (int64_t i = 0; i < nx; ++i) {
+        me->area[i] = dx;
+        me->delta[i] = 2.0 * dx / 2.0;
+        me->nbr[i * 2 + 0] = i - 1;
+        me->fnx[i * 2 + 0] = -1.0;
+        me->flen[i * 2 + 0] = 1.0;
+        me->fbc[i * 2 + 0] = bc_left;
+        me->nbr[i * 2 + 1] = (i + 1 < nx) ? i + 1 : -1;
+        me->fnx[i * 2 + 1] = 1.0;
+        me->flen[i * 2 + 1] = 1.0;
+        me->fbc[i * 2 + 1] = bc_right;
+    }
+    return me;
+}
+
+/* nx x ny rectangles on [x0,x1] x [y0,y1], cell (i,j) at index j*nx + i.
+ * bc = {x-, x+, y-, y+}. */
+or_mesh *or_mesh_2d(int64_t nx, int64_t ny, double x0, double x1, double y0, double y1,
+                    const int *bc)
+{
+    or_mesh *me = mesh_alloc(nx * ny, 4, 2);
+    double dx = (x1 - x0) / (double)nx, dy = (y1 - y0) / (double)ny;
+    for (int64_t j = 0; j < ny; ++j)
+        for (int64_t i = 0; i < nx; ++i) {
+            int64_t c = j * nx + i, f = c * 4;
+            me->area[c] = dx * dy;
+            me->delta[c] = 2.0 * dx * dy / (2.0 * dx + 2.0 * dy);
+            me->nbr[f + 0] = i > 0 ? c - 1 : -1;
+            me->fnx[f + 0] = -1.0; me->fny[f + 0] = 0.0; me->flen[f + 0] = dy; me->fbc[f + 0] = bc[0];
+            me->nbr[f + 1] = i + 1 < nx ? c + 1 : -1;
+            me->fnx[f + 1] = 1.0; me->fny[f + 1] = 0.0; me->flen[f + 1] = dy; me->fbc[f + 1] = bc[1];
+            me->nbr[f + 2] = j > 0 ? c - nx : -1;
+            me->fnx[f + 2] = 0.0; me->fny[f + 2] = -1.0; me->flen[f + 2] = dx; me->fbc[f + 2] = bc[2];
+            me->nbr[f + 3] = j + 1 < ny ? c + nx : -1;
+            me->fnx[f + 3] = 0.0; me->fny[f + 3] = 1.0; me->flen[f + 3] = dx; me->fbc[f + 3] = bc[3];
+        }
+    return me;
+}
+
+typedef struct {
+    int64_t a, b; /* sorted vertex pair */
+    int64_t cell;
+    int face;
+} half_edge;
+
+static int cmp_half_edge(const void *x, const void *y)
+{
+    const half_edge *p = (const half_edge *)x, *q = (const half_edge *)y;
+    if (p->a != q->a) return p->a < q->a ? -1 : 1;
+    if (p->b != q->b) return p->b < q->b ? -1 : 1;
+    return 0;
+}
+
+/* Triangles (vertex indices into verts_xy[2*nverts]); every boundary edge gets kind bc. */
+or_mesh *or_mesh_tri(int64_t nverts, const double *xy, int64_t ntris, const int32_t *tris, int bc)
+{
+    or_mesh *me = mesh_alloc(ntris, 3, 2);
+    half_edge *he = (half_edge *)malloc(sizeof(half_edge) * 3 * ntris);
+    for (int64_t t = 0; t < ntris; ++t) {
+        int64_t v[3] = {tris[3 * t], tris[3 * t + 1], tris[3 * t + 2]};
+        double sa = 0.5 * ((xy[2 * v[1]] - xy[2 * v[0]]) * (xy[2 * v[2] + 1] - xy[2 * v[0] + 1]) -
+                           (xy[2 * v[2]] - xy[2 * v[0]]) * (xy[2 * v[1] + 1] - xy[2 * v[0] + 1]));
+        if (sa < 0.0) { /* make the triangle counter-clockwise */
+            int64_t tmp = v[1];
+            v[1] = v[2];
+            v[2] = tmp;
+            sa = -sa;
+        }
+        double per = 0.0;
+        for (int f = 0; f < 3; ++f) {
+            int64_t p = v[f], q = v[(f + 1) % 3];
+            double ex = xy[2 * q] - xy[2 * p], ey = xy[2 * q + 1] - xy[2 * p + 1];
+            double len = sqrt(ex * ex + ey * ey);
+            me->fnx[t * 3 + f] = ey / len; /* outward normal of a CCW edge p->q */
+            me->fny[t * 3 + f] = -ex / len;
+            me->flen[t * 3 + f] = len;
+            me->fbc[t * 3 + f] = bc;
+            me->nbr[t * 3 + f] = -1;
+            per += len;
+            he[3 * t + f].a = p < q ? p : q;
+            he[3 * t + f].b = p < q ? q : p;
+            he[3 * t + f].cell = t;
+            he[3 * t + f].face = f;
+        }
+        me->area[t] = sa;
+        me->delta[t] = 2.0 * sa / per;
+    }
+    qsort(he, 3 * ntris, sizeof(half_edge), cmp_half_edge);
+    for (int64_t e = 0; e + 1 < 3 * ntris; ++e) {
+        if (he[e].a == he[e + 1].a && he[e].b == he[e + 1].b) {
+            me->nbr[he[e].cell * 3 + he[e].face] = he[e + 1].cell;
+            me->nbr[he[e + 1].cell * 3 + he[e + 1].face] = he[e].cell;
+            ++e;
+        }
+    }
+    free(he);
+    (void)nverts;
+    return me;
+}
+
+/* Geometry accessors (for the tests). */
+void or_mesh_geometry(const or_mesh *me, double *area, double *delta, int64_t *nbr, double *fnx,
+                      double *fny, double *flen)
+{
+    memcpy(area, me->area, sizeof(double) * me->nc);
+    memcpy(delta, me->delta, sizeof(double) * me->nc);
+    memcpy(nbr, me->nbr, sizeof(int64_t) * me->nc * me->nf);
+    memcpy(fnx, me->fnx, sizeof(double) * me->nc * me->nf);
+    memcpy(fny, me->fny, sizeof(double) * me->nc * me->nf);
+    memcpy(flen, me->flen, sizeof(double) * me->nc * me->nf);
+}
+
+/* ------------------------------------------------------------------------- */
+/* The finite-volume step                                                      */
+/* ------------------------------------------------------------------------- */
+
+static void gather(const double *Q, int64_t nc, int nv, int64_t i, double *q)
+{
+    for (int v = 0; v < nv; ++v) q[v] = Q[(int64_t)v * nc + i];
+}
+
+/* Ghost state across a boundary face: transmissive copies the cell; a wall keeps h
+ * and reflects every velocity-moment vector, a_k -> a_k - 2 (a_k . n) n. */
+static void ghost(const or_model *md, const double *qi, int bc, double nx, double ny, double *qg)
+{
+    for (int v = 0; v < md->nv; ++v) qg[v] = qi[v];
+    if (bc != 1) return;
+    for (int k = 0; k < md->m; ++k) {
+        if (md->dim == 1) {
+            qg[ia(md, k)] = -qi[ia(md, k)];
+        } else {
+            double a = qi[ia(md, k)], b = qi[ib(md, k)];
+            double an = a * nx + b * ny;
+            qg[ia(md, k)] = a - 2.0 * an * nx;
+            qg[ib(md, k)] = b - 2.0 * an * ny;
+        }
+    }
+}
+
+/* Hydrostatic reconstruction of a cell state against the face bed level bf:
+ * h* = max(0, h + b - bf), velocities kept (zero if h <= h_dry or h* <= h_dry). */
+static void hydrostatic_state(const or_model *md, const double *q, double b, double bf, double *qs)
+{
+    double al[OR_MAXM], be[OR_MAXM];
+    velocities(md, q, al, be);
+    double hs = q[0] + b - bf;
+    if (hs < 0.0) hs = 0.0;
+    for (int v = 0; v < md->nv; ++v) qs[v] = 0.0;
+    qs[0] = hs;
+    if (!(hs > md->h_dry)) return;
+    for (int k = 0; k < md->m; ++k) {
+        qs[ia(md, k)] = hs * al[k];
+        if (md->dim == 2) qs[ib(md, k)] = hs * be[k];
+    }
+}
+
+/* The face term of reading R6, seen from cell i (outward normal n, length len is
+ * applied by the caller):  1/2(F_n(Qi*)+F_n(Qj*)) - 1/2 s_f (Qj*-Qi*) - P(hi*) n
+ *                         + 1/2 Btilde_n (Qj*-Qi*). */
+static void face_term(const or_model *md, const double *qi, double bi, const double *qj,
+                      double bj, double nx, double ny, double *out)
+{
+    int nv = md->nv;
+    double bf = bi > bj ? bi : bj;
+    double qsi[OR_MAXV], qsj[OR_MAXV], Fi[OR_MAXV], Fj[OR_MAXV], dq[OR_MAXV];
+    hydrostatic_state(md, qi, bi, bf, qsi);
+    hydrostatic_state(md, qj, bj, bf, qsj);
+    or_flux(md, qsi, nx, ny, Fi);
+    or_flux(md, qsj, nx, ny, Fj);
+    double si = or_wavespeed(md, qsi), sj = or_wavespeed(md, qsj);
+    double sf = si > sj ? si : sj;
+    for (int v = 0; v < nv; ++v) {
+        dq[v] = qsj[v] - qsi[v];
+        out[v] = 0.5 * (Fi[v] + Fj[v]) - 0.5 * sf * dq[v];
+    }
+    double p = 0.5 * md->g * qsi[0] * qsi[0];
+    out[ia(md, 0)] -= p * nx;
+    if (md->dim == 2) out[ib(md, 0)] -= p * ny;
+
+    /* 3-point Gauss-Legendre on [0,1] along Psi(s) = Qi* + s (Qj* - Qi*) */
+    const double sq[3] = {0.5 - sqrt(15.0) / 10.0, 0.5, 0.5 + sqrt(15.0) / 10.0};
+    const double wq[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+    double Bt[OR_MAXV * OR_MAXV], Bq[OR_MAXV * OR_MAXV], psi[OR_MAXV];
+    for (int v = 0; v < nv * nv; ++v) Bt[v] = 0.0;
+    for (int q = 0; q < 3; ++q) {
+        for (int v = 0; v < nv; ++v) psi[v] = qsi[v] + sq[q] * dq[v];
+        or_nc_matrix(md, psi, nx, ny, Bq);
+        for (int v = 0; v < nv * nv; ++v) Bt[v] += wq[q] * Bq[v];
+    }
+    for (int r = 0; r < nv; ++r) {
+        double acc = 0.0;
+        for (int c = 0; c < nv; ++c) acc += Bt[r * nv + c] * dq[c];
+        out[r] += 0.5 * acc;
+    }
+}
+
+/* One explicit stage Y = R(X + dt L(X)) (readings R5, R6). */
+void or_stage(const or_model *md, const or_mesh *me, const double *X, const double *bed, double dt,
+              double *Y)
+{
+    int nv = md->nv;
+    int64_t nc = me->nc;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < nc; ++i) {
+        double qi[OR_MAXV], qj[OR_MAXV], term[OR_MAXV], acc[OR_MAXV], S[OR_MAXV], y[OR_MAXV];
+        gather(X, nc, nv, i, qi);
+        double bi = bed ? bed[i] : 0.0;
+        for (int v = 0; v < nv; ++v) acc[v] = 0.0;
+        for (int f = 0; f < me->nf; ++f) {
+            int64_t e = i * me->nf + f;
+            double nx = me->fnx[e], ny = me->fny[e], bj;
+            int64_t j = me->nbr[e];
+            if (j >= 0) {
+                gather(X, nc, nv, j, qj);
+                bj = bed ? bed[j] : 0.0;
+            } else {
+                ghost(md, qi, me->fbc[e], nx, ny, qj);
+                bj = bi;
+            }
+            face_term(md, qi, bi, qj, bj, nx, ny, term);
+            for (int v = 0; v < nv; ++v) acc[v] += me->flen[e] * term[v];
+        }
+        or_source_newtonian(md, qi, S);
+        for (int v = 0; v < nv; ++v) y[v] = qi[v] - dt / me->area[i] * acc[v] + dt * S[v];
+        or_bottom_friction(md, y, dt);
+        for (int v = 0; v < nv; ++v) Y[(int64_t)v * nc + i] = y[v];
+    }
+}
+
+double or_max_wavespeed(const or_model *md, const or_mesh *me, const double *Q)
+{
+    double smax = 0.0;
+    double q[OR_MAXV];
+    for (int64_t i = 0; i < me->nc; ++i) {
+        gather(Q, me->nc, md->nv, i, q);
+        double s = or_wavespeed(md, q);
+        if (s > smax || s != s) smax = s;
+    }
+    return smax;
+}
+
+double or_min_delta(const or_mesh *me)
+{
+    double d = me->delta[0];
+    for (int64_t i = 1; i < me->nc; ++i)
+        if (me->delta[i] < d) d = me->delta[i];
+    return d;
+}
+
+/* Time step of reading R7 for the state Q. */
+double or_cfl_dt(const or_model *md, const or_mesh *me, const double *Q, double cfl)
+{
+    return cfl * or_min_delta(me) / or_max_wavespeed(md, me, Q);
+}
+
+/* nsteps SSP-RK2 steps: Q1 = stage(Qn), Q2 = stage(Q1), Qn+1 = (Qn + Q2)/2.
+ * dt_fixed > 0 uses that step; dt_fixed <= 0 recomputes dt from Qn every step.
+ * Q is [nv][nc]; bed may be NULL (flat).  Returns the time advanced in *t_out. */
+int or_step(const or_model *md, const or_mesh *me, double *Q, const double *bed, double dt_fixed,
+            double cfl, int nsteps, double *t_out)
+{
+    int64_t n = (int64_t)md->nv * me->nc;
+    double *Q1 = (double *)malloc(sizeof(double) * n);
+    double *Q2 = (double *)malloc(sizeof(double) * n);
+    double t = 0.0;
+    for (int s = 0; s < nsteps; ++s) {
+        double dt = dt_fixed > 0.0 ? dt_fixed : or_cfl_dt(md, me, Q, cfl);
+        or_stage(md, me, Q, bed, dt, Q1);
+        or_stage(md, me, Q1, bed, dt, Q2);
+        for (int64_t k = 0; k < n; ++k) Q[k] = 0.5 * (Q[k] + Q2[k]);
+        t += dt;
+    }
+    free(Q1);
+    free(Q2);
+    if (t_out) *t_out = t;
+    return 0;
+}
+
+/* Total mass sum_i |Omega_i| h_i (FP64). */
+double or_mass(const or_mesh *me, const double *Q)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < me->nc; ++i) s += me->area[i] * Q[i];
+    return s;
+}
+
+int or_max_level(void) { return OR_MAXN; }

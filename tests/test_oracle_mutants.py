@@ -1,0 +1,52 @@
+"""The oracle's pins are sensitive: each plausible mistake, planted in a copy of the
+oracle's C source on the CPU, makes at least one of the oracle pin tests fail.
+
+Every mutant below changes one term of the scheme (a sign, an index order, a
+dropped term, a wrong bed level, a wrong factor).  The copy is compiled into a
+temporary directory and the pin suite is run against it in a subprocess.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "zoomy_oracle.c")
+
+MUTANTS = {
+    "nc_sign": ("double ea = (k == l) ? -al[0] : 0.0;", "double ea = (k == l) ? al[0] : 0.0;"),
+    "nc_index_order": ("ea += al[j] * md->B[(k * m + j) * m + l] / md->M[k];",
+                       "ea += al[j] * md->B[(k * m + l) * m + j] / md->M[k];"),
+    "nc_y_dropped": ("Bn[ib(md, k) * nv + ib(md, l)] += ny * eb;", "(void)eb;"),
+    "pressure_correction_dropped": ("out[ia(md, 0)] -= p * nx;", "(void)p;"),
+    "bed_min_instead_of_max": ("double bf = bi > bj ? bi : bj;", "double bf = bi < bj ? bi : bj;"),
+    "dissipation_dropped": ("out[v] = 0.5 * (Fi[v] + Fj[v]) - 0.5 * sf * dq[v];", "out[v] = 0.5 * (Fi[v] + Fj[v]);"),
+    "newtonian_sign": ("S[ia(md, k)] = -(md->nu / (md->rho * h)) * sa / md->M[k];",
+                       "S[ia(md, k)] = (md->nu / (md->rho * h)) * sa / md->M[k];"),
+    "slip_weight_without_2k1": ("double w = md->phi0[k] / md->M[k];", "double w = md->phi0[k];"),
+    "wavespeed_drops_higher_moments": ("if (k >= 2) s1 += sqrt(ak2);", "(void)s1;"),
+    "wall_not_reflecting": ("if (bc != 1) return;", "return;"),
+    "flux_moment_mass_matrix": ("F[ia(md, k)] = nx * (h * saa / md->M[k] + p);", "F[ia(md, k)] = nx * (h * saa + p);"),
+    "rk2_average_dropped": ("for (int64_t k = 0; k < n; ++k) Q[k] = 0.5 * (Q[k] + Q2[k]);",
+                           "for (int64_t k = 0; k < n; ++k) Q[k] = Q2[k];"),
+    "hr_depth_not_clipped": ("if (hs < 0.0) hs = 0.0;", "(void)0;"),
+}
+
+PIN_TESTS = ["tests/test_oracle_basis.py", "tests/test_oracle_model.py", "tests/test_oracle_scheme.py"]
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site for {name} not found exactly once"
+    mutated = tmp_path / "mutant.c"
+    mutated.write_text(src.replace(old, new))
+    so = tmp_path / "libmutant.so"
+    subprocess.run(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC", "-shared", str(mutated),
+                    "-o", str(so), "-lm"], check=True, capture_output=True)
+    env = dict(os.environ, ZOOMY_ORACLE_LIB=str(so), OMP_NUM_THREADS="2")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PIN_TESTS],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode != 0, f"mutant {name} passed every pin:\n{r.stdout[-2000:]}"
