@@ -1,0 +1,335 @@
+"""Benchmark: fused SSP-RK2 finite-volume step of the level-2 shallow-moment model on a
+2048 x 2048 structured grid (7 variables, FP32 state), one JSON line on rank 0.
+
+Workload (seeded, synthetic): Gaussian surface bump (amplitude U[0.1, 0.5], sigma 0.05) on a
+lake of level 1 over an 8-mode Fourier bathymetry of amplitude 0.2, wall boundaries, Navier slip
+C = 0.1 with Newtonian nu = 0.01, adaptive CFL 0.45 step computed on the device.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the baseline of this port) on the host cores on a
+bounded window of the same workload.  For N > 1 (torchrun) every rank runs an independent replica
+of the workload (the step has no data-parallel split on one grid in this build): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_SIDE = 2048
+LEVEL = 2
+NV = 2 * LEVEL + 3
+FRIC = dict(kind=1, C=0.1, nu=0.01)
+CFL = 0.45
+# algorithmic bytes per cell and launch (FP32): stage 1 reads Q^n (7) + b, writes Q1 (7);
+# stage 2 reads Q1 (7) + b + Q^n (7), writes Q^{n+1} (7)
+BYTES_STAGE = {1: 4 * (NV + 1 + NV), 2: 4 * (NV + 1 + NV + NV)}
+METRIC = "cell-updates/sec and % of HBM peak per FV step"
+KERNEL_SOURCES = ["paper_2601_04826_gb300/csrc/fv_struct.cu", "paper_2601_04826_gb300/csrc/model.cuh",
+                  "paper_2601_04826_gb300/csrc/fv_common.cuh", "paper_2601_04826_gb300/csrc/basis.cuh"]
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic():
+    """DRAM bytes per stage-2 launch from the committed ncu summary, if it was taken on this kernel source."""
+    d = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(d):
+        return None
+    want = kernel_hash()
+    for fn in sorted(os.listdir(d)):
+        if not fn.endswith((".md", ".txt")):
+            continue
+        for line in open(os.path.join(d, fn)):
+            m = re.search(r"traffic_per_launch_bytes:\s*([0-9.eE+]+)\s+source_hash:\s*([0-9a-f]+)", line)
+            if m and m.group(2) == want:
+                return float(m.group(1))
+    return None
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        loaded = [s for s, _, _ in rows]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(m for _, m, _ in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def workload():
+    from paper_2601_04826_gb300 import inputs
+
+    Q0, b = inputs.gaussian_bump_2d(N_SIDE, N_SIDE, LEVEL, seed=0)
+    return Q0, b
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_2601_04826_gb300 import build, zoomy
+
+    if rank == 0 or not os.path.exists(zoomy.LIB_PATH):
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    Q0, b = workload()
+    nc = N_SIDE * N_SIDE
+    fr = zoomy.friction(FRIC["kind"], C=FRIC["C"], nu=FRIC["nu"])
+    ctx = zoomy.Context(zoomy.mesh_2d(N_SIDE, N_SIDE, bathymetry=b), LEVEL, fr, cfl=CFL, dtype=zoomy.FP32)
+    Q = torch.tensor(Q0, dtype=torch.float32, device=dev)
+
+    # warm-up
+    ctx.step(Q, nsteps=args.warmup, dt=0.0)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        zoomy.zoomy_profile_enable(ctx.ctx, True)
+        e0.record(stream)
+        ctx.step(Q, nsteps=args.steps, dt=0.0, sync=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    t_sim = zoomy.zoomy_sync(ctx.ctx)  # raises on a device-detected error
+    launches, kms = zoomy.zoomy_profile_read(ctx.ctx)
+    zoomy.zoomy_profile_enable(ctx.ctx, False)
+    ms = e0.elapsed_time(e1)
+    ms_t = torch.tensor([ms], device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms = float(ms_t.item())
+
+    # end-to-end through the host-buffer entry point: H2D of the state, one step, D2H of the result
+    Qh = torch.tensor(Q0, dtype=torch.float32).pin_memory()
+    ctx.step_host(Qh, nsteps=1, dt=0.0)
+    n_e2e = max(3, min(args.steps, 30))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        ctx.step_host(Qh, nsteps=1, dt=0.0)
+    e2e_s = (time.perf_counter() - t0) / n_e2e
+    e2e_t = torch.tensor([e2e_s], device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
+    e2e_s = float(e2e_t.item())
+    ctx.close()
+
+    if rank != 0:
+        return None
+    hbm, peak_kind = peaks()
+    avg2 = kms[1] / max(launches[1], 1)
+    avg1 = kms[0] / max(launches[0], 1)
+    dom = 2 if avg2 >= avg1 else 1
+    avg = avg2 if dom == 2 else avg1
+    achieved = BYTES_STAGE[dom] * nc / (avg * 1e-3) / 1e9
+    traffic = ncu_traffic() if dom == 2 else None
+    value = world * nc * args.steps / (ms * 1e-3)
+    step_bytes = (BYTES_STAGE[1] + BYTES_STAGE[2]) * nc
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "cell-updates/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded Gaussian bump over 8-mode Fourier bathymetry)",
+        "config": {"workload": "2D shallow-moment level 2, 2048x2048 structured grid, 7 vars, FP32 state, walls, "
+                               "slip C=0.1 + Newtonian nu=0.01, SSP-RK2, adaptive CFL 0.45",
+                   "cells": nc, "level": LEVEL, "global_batch": world, "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (Q 117 MB + stage buffer 117 MB + bed 17 MB per replica)",
+                   "step_hbm_fraction": step_bytes / (ms / args.steps * 1e-3) / 1e9 / hbm,
+                   "sim_time_advanced": t_sim},
+        "roofline": {"bound": "hbm", "kernel": f"k_stage_2d<2,float,{dom}>", "achieved": achieved, "peak": hbm,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": BYTES_STAGE[dom] * nc,
+                     "avg_launch_ms": {"stage1": avg1, "stage2": avg2}},
+        "e2e": {"value": nc / e2e_s * world, "unit": "cell-updates/s", "h2d_bytes_per_step": 4 * NV * nc,
+                "d2h_bytes_per_step": 4 * NV * nc},
+        "gpu_launches": int(launches[0] + launches[1] + 1),
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args)
+    return line
+
+
+def oracle_window_run(side, nsteps):
+    """The oracle on a side x side window of the workload (cells of the 2048^2 grid, walls)."""
+    import numpy as np
+
+    from oracle import oracle as O
+
+    Q0, b = workload()
+    Q0 = Q0.astype(np.float32).astype(np.float64)
+    b = b.astype(np.float32).astype(np.float64)
+    if side < N_SIDE:
+        # window centred on the bump's centre region
+        j0 = i0 = (N_SIDE - side) // 2
+        idx = (np.arange(j0, j0 + side)[:, None] * N_SIDE + np.arange(i0, i0 + side)[None, :]).reshape(-1)
+        Q0 = Q0[:, idx]
+        b = b[idx]
+    h = 1.0 / N_SIDE
+    md = O.Model(LEVEL, 2, g=9.81, h_dry=1e-6, friction=FRIC["kind"], C=FRIC["C"], nu=FRIC["nu"])
+    mesh = O.Mesh.rect(side, side, 0, side * h, 0, side * h, bc=(1, 1, 1, 1))
+    t0 = time.perf_counter()
+    O.step(md, mesh, Q0, nsteps, dt=0.0, cfl=CFL, bed=b)
+    return time.perf_counter() - t0
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(args):
+    side, nsteps = N_SIDE, 2
+    secs = oracle_window_run(side, nsteps)
+    threads = int(os.environ.get("OMP_NUM_THREADS", host_cores()))
+    return {"value": side * side * nsteps / secs, "unit": "cell-updates/s", "cores": threads, "kind": "oracle",
+            "sample": f"{nsteps} SSP-RK2 steps of the full {side}x{side} level-2 workload, FP64 C oracle, OpenMP "
+                      f"over cells, {secs:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    # window sized so that warmup + steps end within about two minutes
+    probe_side = 256
+    t = oracle_window_run(probe_side, 1)
+    per_cell = t / (probe_side * probe_side)
+    budget = 110.0
+    cells = budget / max(args.steps + args.warmup, 1) / per_cell
+    side = int(max(32, min(N_SIDE, cells ** 0.5)))
+    if args.warmup:
+        oracle_window_run(side, args.warmup)
+    t0 = time.perf_counter()
+    oracle_window_run(side, args.steps)
+    secs = time.perf_counter() - t0
+    value = side * side * args.steps / secs
+    threads = int(os.environ.get("OMP_NUM_THREADS", host_cores()))
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded Gaussian bump over 8-mode Fourier bathymetry)",
+            "config": {"workload": "2D shallow-moment level 2, 2048x2048 structured grid, 7 vars, walls, "
+                                   "slip C=0.1 + Newtonian nu=0.01, SSP-RK2, adaptive CFL 0.45",
+                       "window": f"{side}x{side} cells of the 2048^2 workload per step"},
+            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{side}x{side} window, {args.steps} SSP-RK2 steps"},
+            "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch
+
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        line = run_ours(args, rank, world, local_rank)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1 and args.impl == "ours":
+        import torch
+
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

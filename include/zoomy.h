@@ -1,0 +1,165 @@
+/*
+ * zoomy.h -- C ABI of the GB300 finite-volume library for the shallow-water (level 0) to
+ * shallow-moment (level N) hierarchy.
+ *
+ * The library advances   d_t Q + div F(Q) + B(Q) grad Q = S(Q)    (Eq. (PDE-structure), Sec. 1)
+ * for the shallow-moment system of Eq. (sme) (1D) and its 2D form in Sec. 3.4, with the explicit
+ * path-conservative finite-volume step named in Sec. 2.1.2 ("hyperbolic_step", after Dumbser,
+ * Enaux & Toro 2008 and Castro et al. 2009), hydrostatic reconstruction at the bed, the slip /
+ * Newtonian friction closure of Sec. 3.4 (plus Manning), wet/dry handling, SSP-RK2 stages and the
+ * adaptive CFL step of the Sec. 3.1 runner (timestepping.adaptive(CFL=0.45)).
+ *
+ * State layout (every entry point): Q is structure-of-arrays, Q[v * ld + i] for variable v and
+ * cell i, with ld >= number of cells.  Variable order:
+ *   1D: (h, h alpha_0, h alpha_1, ..., h alpha_N)                       nv = N + 2
+ *   2D: (h, h alpha_0, h beta_0, h alpha_1..h alpha_N, h beta_1..h beta_N) nv = 2N + 3
+ * where alpha_k / beta_k are the Legendre moments of the x / y velocity (alpha_0 = mean u).
+ * Element type: float (dtype 0) or double (dtype 1), as set by zoomy_model_set.
+ * Structured 2D cells are numbered j * nx + i; triangle meshes use the library's cell order
+ * (see zoomy_mesh_permutation).
+ *
+ * Ownership: descriptors and host arrays passed in are read during the call only.  Q buffers are
+ * owned by the caller.  The context owns its device copies of the mesh, the bed, the stage buffer
+ * and the reduction scalars; zoomy_mesh_destroy frees them.
+ *
+ * Streams: all device work of a context is ordered on its stream (zoomy_mesh_create /
+ * zoomy_set_stream).  Calls that return a host value synchronise that stream.
+ *
+ * Errors: every call returns a zoomy_status and never aborts.  Invalid arguments are rejected
+ * before any device work.  zoomy_last_error() describes the last failure of the calling thread.
+ */
+#ifndef ZOOMY_H
+#define ZOOMY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ZOOMY_OK = 0,
+    ZOOMY_EINVAL = 1,     /* invalid argument (checked before any launch) */
+    ZOOMY_ENOMEM = 2,     /* device or host allocation failed */
+    ZOOMY_ECUDA = 3,      /* CUDA runtime error; see zoomy_last_error() */
+    ZOOMY_ENAN = 4,       /* a step produced a non-finite state */
+    ZOOMY_ENEGDEPTH = 5,  /* a step produced a negative depth */
+    ZOOMY_ECFL = 6,       /* no positive finite wave speed: the CFL step is undefined */
+    ZOOMY_ETIMEOUT = 7,   /* a device-side wait gave up (persistent ensemble kernel) */
+    ZOOMY_ESTATE = 8      /* call out of order (e.g. zoomy_step before zoomy_model_set) */
+} zoomy_status;
+
+typedef struct zoomy_ctx zoomy_ctx; /* opaque, library-owned */
+
+enum { ZOOMY_MESH_1D = 0, ZOOMY_MESH_2D = 1, ZOOMY_MESH_TRI = 2 };
+enum { ZOOMY_BC_TRANSMISSIVE = 0, ZOOMY_BC_WALL = 1 };
+enum { ZOOMY_FRICTION_NONE = 0, ZOOMY_FRICTION_SLIP_NEWTONIAN = 1, ZOOMY_FRICTION_MANNING = 2 };
+enum { ZOOMY_FP32 = 0, ZOOMY_FP64 = 1 };
+
+/* Mesh description (caller-owned, read during zoomy_mesh_create only).
+ *   kind ZOOMY_MESH_1D : nx uniform cells on [x0, x1]; bc[0] left, bc[1] right.
+ *   kind ZOOMY_MESH_2D : nx * ny rectangles on [x0,x1] x [y0,y1]; bc = {x-, x+, y-, y+}.
+ *   kind ZOOMY_MESH_TRI: ntris triangles over nverts vertices (verts_xy[2*nverts], tris[3*ntris],
+ *                        host memory, either orientation); every boundary edge takes bc[0].
+ * bathymetry: host array of the bed level b per cell in the caller's cell numbering, or NULL
+ * for a flat bed.  morton_reorder (triangles only): 1 = number the cells along a Morton curve of
+ * their centroids for locality of the neighbour gathers. */
+typedef struct {
+    int32_t kind;
+    int64_t nx, ny;
+    double x0, x1, y0, y1;
+    int32_t bc[4];
+    int64_t nverts, ntris;
+    const double *verts_xy;
+    const int32_t *tris;
+    const double *bathymetry;
+    int32_t morton_reorder;
+} zoomy_mesh_desc;
+
+/* Friction closure (Sec. 3.4): Navier slip at the bed sigma|_0 = C u|_0 with the Newtonian bulk
+ * stress sigma = nu d_z u (kind SLIP_NEWTONIAN), or the Manning bottom stress g n^2 |u_b| u_b /
+ * h^(1/3) (kind MANNING, parameter manning_n).  rho divides the stresses (kinematic: rho = 1). */
+typedef struct {
+    int32_t kind;
+    double C, nu, rho, manning_n;
+} zoomy_friction;
+
+/* Version of the C ABI (major * 10000 + minor * 100 + patch). */
+int32_t zoomy_version(void);
+
+/* Create a context for a mesh.  stream: a cudaStream_t (NULL = legacy default stream) on which
+ * all device work of the context is queued.  On success *out receives the context. */
+zoomy_status zoomy_mesh_create(const zoomy_mesh_desc *desc, void *stream, zoomy_ctx **out);
+
+/* Free the context and every device buffer it owns.  NULL is accepted. */
+zoomy_status zoomy_mesh_destroy(zoomy_ctx *ctx);
+
+/* Change the stream of the context. */
+zoomy_status zoomy_set_stream(zoomy_ctx *ctx, void *stream);
+
+/* Number of cells and min_i Delta_i with Delta_i = 2 |Omega_i| / P_i (the CFL length). */
+zoomy_status zoomy_mesh_info(zoomy_ctx *ctx, int64_t *ncells, double *min_delta);
+
+/* Cell permutation of a triangle mesh: perm_out[new] = caller's index (host, ncells int64).
+ * Structured meshes return the identity. */
+zoomy_status zoomy_mesh_permutation(zoomy_ctx *ctx, int64_t *perm_out);
+
+/* Select the model: level N in [0, 4] (Eq. (sme)), friction closure (may be NULL = none),
+ * gravity g > 0, CFL number cfl in (0, 1], dry threshold h_dry >= 0 (velocities are zero where
+ * h <= h_dry), dtype ZOOMY_FP32 (FP32 state and flux; FP64-exact bed/surface differences; FP64
+ * mass sums) or ZOOMY_FP64.  Allocates the stage buffer. */
+zoomy_status zoomy_model_set(zoomy_ctx *ctx, int32_t level, const zoomy_friction *friction, double g, double cfl,
+                             double h_dry, int32_t dtype);
+
+/* Number of variables nv of the current model. */
+zoomy_status zoomy_nvars(zoomy_ctx *ctx, int32_t *nv);
+
+/* Advance Q (device pointer, SoA [nv][ld], dtype of the model) by nsteps SSP-RK2 steps:
+ *   Q1 = R(Q^n + dt L(Q^n)),  Q^{n+1} = 1/2 (Q^n + R(Q1 + dt L(Q1)))
+ * dt > 0: fixed step.  dt == 0: dt = cfl * min Delta / max_i s_i(Q^n), recomputed on the device
+ * every step (no host round trip).  Q is updated in place.
+ * t_advanced (host) != NULL: the stream is synchronised, *t_advanced receives the simulated time
+ * advanced since the last status read (see zoomy_sync) and device-detected errors are returned (ZOOMY_ENAN / ZOOMY_ENEGDEPTH / ZOOMY_ECFL; Q then
+ * holds the state after the step that raised it, and the later steps of the call are skipped).
+ * t_advanced == NULL: the call only queues work; zoomy_sync reports the outcome. */
+zoomy_status zoomy_step(zoomy_ctx *ctx, void *Q, int64_t ld, double dt, int32_t nsteps, double *t_advanced);
+
+/* Same step with Q in HOST memory (pinned for full copy speed): copies Q to a context-owned
+ * device buffer, steps, copies the result back, synchronises. */
+zoomy_status zoomy_step_host(zoomy_ctx *ctx, void *Q_host, int64_t ld, double dt, int32_t nsteps,
+                             double *t_advanced);
+
+/* Wait for the queued steps; *t_total (may be NULL) receives the time advanced by all steps
+ * queued since the last status read (a zoomy_step with t_advanced, zoomy_step_host or
+ * zoomy_sync), and the first device-detected error among them is returned.  An error is sticky:
+ * once raised, later queued steps are skipped until it is read here. */
+zoomy_status zoomy_sync(zoomy_ctx *ctx, double *t_total);
+
+/* max_i s_i(Q) (device Q, synchronises): s = |u_mean| + sqrt(g h + sum_{k>=1}|a_k|^2) +
+ * sum_{k>=2}|a_k|, the bound on the spectral radius of the quasilinear matrix (Sec. 2.1.1,
+ * eigenstructure of A . n) used for the CFL step. */
+zoomy_status zoomy_max_wavespeed(zoomy_ctx *ctx, const void *Q, int64_t ld, double *out);
+
+/* sum_i |Omega_i| h_i accumulated in FP64 in a fixed order (device Q, synchronises). */
+zoomy_status zoomy_mass(zoomy_ctx *ctx, const void *Q, int64_t ld, double *out);
+
+/* Work decomposition of the structured 2D kernels (a performance knob; results do not depend
+ * on it): each warp marches over rows_per_warp rows of a 30-column strip, warps_per_block warps
+ * per CTA.  rows_per_warp in [1, 4096], warps_per_block in [1, 32]. */
+zoomy_status zoomy_tune_set(zoomy_ctx *ctx, int32_t rows_per_warp, int32_t warps_per_block);
+
+/* Per-launch timing of the stage kernels with CUDA events recorded on the context's stream
+ * around every stage launch (on = 1) or off (on = 0, default).  zoomy_profile_read waits for
+ * the stream and returns the launch counts and the summed device time in milliseconds of the
+ * stage-1 and stage-2 kernels since profiling was enabled, then resets the counters.  Arrays
+ * of length 2 (host). */
+zoomy_status zoomy_profile_enable(zoomy_ctx *ctx, int32_t on);
+zoomy_status zoomy_profile_read(zoomy_ctx *ctx, int64_t *launches, double *total_ms);
+
+/* Text of the last error of the calling thread (static storage, never NULL). */
+const char *zoomy_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ZOOMY_H */

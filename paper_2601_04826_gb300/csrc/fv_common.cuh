@@ -1,0 +1,107 @@
+// fv_common.cuh -- device control block, variable layout and kernel arguments shared by the
+// structured-grid kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "model.cuh"
+
+namespace zoomy {
+
+// Per-context device control block (one per zoomy_ctx, device memory).
+struct DevCtl {
+    unsigned int smax_f[2];          // max wave speed, FP32 bit pattern (s >= 0 orders like uint)
+    unsigned long long smax_d[2];    // max wave speed, FP64 bit pattern
+    double t;                        // time advanced by the steps of the current call
+    double dt_last;                  // last step size
+    unsigned int status;             // DEV_* flags, sticky until the host clears them
+    unsigned int pad;
+};
+
+enum : unsigned int { DEV_NAN = 1u, DEV_NEGDEPTH = 2u, DEV_NOWAVE = 4u };
+
+// Variable index of h alpha_k / h beta_k in the SoA state (Eq. (sme) variable order).
+template <int N, int D>
+__host__ __device__ constexpr int var_a(int k)
+{
+    return D == 1 ? 1 + k : (k == 0 ? 1 : 2 + k);
+}
+template <int N>
+__host__ __device__ constexpr int var_b(int k)
+{
+    return k == 0 ? 2 : 2 + N + k;
+}
+template <int N, int D>
+__host__ __device__ constexpr int nvars()
+{
+    return D == 1 ? 2 + N : 3 + 2 * N;
+}
+
+template <typename T>
+struct StageArgs {
+    const T *X;     // stage input [nv][ld]
+    const T *Qn;    // Q^n for the final SSP-RK2 average (stage 2), else unused
+    T *out;         // stage output [nv][ld] (stage 2 may alias Qn: pointwise read-then-write)
+    const T *bed;   // [ncells] bed level, or nullptr for a flat bed
+    int64_t ld;
+    int nx, ny;
+    T inv_dx, inv_dy;
+    int bc[4];      // x-, x+, y-, y+ (1D: left, right): 0 transmissive, 1 wall
+    T g, hdry;
+    int fric;       // 0 none, 1 slip + Newtonian, 2 Manning
+    T nu_rho, C_rho, gn2;
+    double cfl, dmin, dt_fixed;  // dt_fixed > 0: fixed step; else CFL from ctl->smax[slot_in]
+    int slot_in, slot_out;
+    DevCtl *ctl;
+    int nstrips, nsegs, H;       // 2D marching decomposition
+};
+
+// Step size of the current step: fixed, or dt = CFL * min Delta / max s (reading of the
+// adaptive time stepping with CFL = 0.45 of Sec. 3.1), s_max taken over Q^n.
+template <typename T>
+__device__ __forceinline__ bool step_dt(const StageArgs<T> &a, T &dt)
+{
+    if (a.dt_fixed > 0.0) {
+        dt = T(a.dt_fixed);
+        return true;
+    }
+    double smax;
+    if constexpr (sizeof(T) == 4)
+        smax = (double)__uint_as_float(*(volatile unsigned int *)&a.ctl->smax_f[a.slot_in]);
+    else
+        smax = __longlong_as_double((long long)*(volatile unsigned long long *)&a.ctl->smax_d[a.slot_in]);
+    if (!(smax > 0.0) || !(smax < 1e300)) return false;
+    dt = T(a.cfl * a.dmin / smax);
+    return true;
+}
+
+// Bookkeeping done once per step by one thread of the first stage.
+template <typename T>
+__device__ __forceinline__ void step_bookkeeping(const StageArgs<T> &a, T dt)
+{
+    a.ctl->t += (double)dt;
+    a.ctl->dt_last = (double)dt;
+    if constexpr (sizeof(T) == 4)
+        a.ctl->smax_f[a.slot_out] = 0u;
+    else
+        a.ctl->smax_d[a.slot_out] = 0ull;
+}
+
+template <typename T>
+__device__ __forceinline__ void reduce_smax(DevCtl *ctl, int slot, T s)
+{
+    // warp max, then one atomic per warp on the bit pattern (s >= 0, or NaN which wins)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        T v = __shfl_xor_sync(0xffffffffu, s, o);
+        s = (v > s || v != v) ? v : s;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if constexpr (sizeof(T) == 4)
+            atomicMax(&ctl->smax_f[slot], __float_as_uint(s));
+        else
+            atomicMax(&ctl->smax_d[slot], (unsigned long long)__double_as_longlong(s));
+    }
+}
+
+}  // namespace zoomy

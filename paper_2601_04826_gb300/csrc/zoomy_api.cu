@@ -1,0 +1,434 @@
+// zoomy_api.cu -- the C ABI of include/zoomy.h: contexts, model selection, the SSP-RK2 step
+// driver (Sec. 2.1.2 "HyperbolicSolver": boundary handling, hyperbolic step and source step
+// inside a time loop with adaptive dt), reductions and error reporting.
+#include <cstdarg>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/zoomy.h"
+#include "fv_common.cuh"
+#include "zoomy_kernels.h"
+#include "zoomy_internal.h"
+
+using namespace zoomy;
+
+static thread_local char g_err[512] = "no error";
+
+zoomy_status zoomy::set_error(zoomy_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+zoomy_status zoomy::cuda_fail(cudaError_t e, const char *where)
+{
+    return set_error(e == cudaErrorMemoryAllocation ? ZOOMY_ENOMEM : ZOOMY_ECUDA, "%s: %s", where,
+                     cudaGetErrorString(e));
+}
+
+#define ZCHECK(call)                                                    \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);             \
+    } while (0)
+
+extern "C" const char *zoomy_last_error(void) { return g_err; }
+
+extern "C" int32_t zoomy_version(void) { return 10000; }
+
+static size_t elem_size(int dtype) { return dtype == ZOOMY_FP64 ? 8 : 4; }
+
+extern "C" zoomy_status zoomy_mesh_create(const zoomy_mesh_desc *d, void *stream, zoomy_ctx **out)
+{
+    if (!d || !out) return set_error(ZOOMY_EINVAL, "zoomy_mesh_create: NULL argument");
+    *out = nullptr;
+    if (d->kind == ZOOMY_MESH_1D || d->kind == ZOOMY_MESH_2D) {
+        if (d->nx < 1 || (d->kind == ZOOMY_MESH_2D && d->ny < 1))
+            return set_error(ZOOMY_EINVAL, "zoomy_mesh_create: nx, ny must be >= 1");
+        if (d->nx > (1LL << 30) || d->ny > (1LL << 30) || (d->kind == ZOOMY_MESH_2D && d->nx * d->ny > (1LL << 40)))
+            return set_error(ZOOMY_EINVAL, "zoomy_mesh_create: grid too large");
+        if (!(d->x1 > d->x0) || (d->kind == ZOOMY_MESH_2D && !(d->y1 > d->y0)))
+            return set_error(ZOOMY_EINVAL, "zoomy_mesh_create: empty domain");
+        int nbc = d->kind == ZOOMY_MESH_1D ? 2 : 4;
+        for (int i = 0; i < nbc; ++i)
+            if (d->bc[i] != ZOOMY_BC_TRANSMISSIVE && d->bc[i] != ZOOMY_BC_WALL)
+                return set_error(ZOOMY_EINVAL, "zoomy_mesh_create: bc[%d] must be 0 or 1", i);
+    } else if (d->kind == ZOOMY_MESH_TRI) {
+        return create_tri_mesh(d, stream, out);
+    } else {
+        return set_error(ZOOMY_EINVAL, "zoomy_mesh_create: unknown mesh kind %d", d->kind);
+    }
+    zoomy_ctx *c = new (std::nothrow) zoomy_ctx();
+    if (!c) return set_error(ZOOMY_ENOMEM, "zoomy_mesh_create: host allocation");
+    c->kind = d->kind;
+    c->dim = d->kind == ZOOMY_MESH_1D ? 1 : 2;
+    c->nx = d->nx;
+    c->ny = d->kind == ZOOMY_MESH_1D ? 1 : d->ny;
+    c->nc = c->nx * c->ny;
+    c->dx = (d->x1 - d->x0) / (double)c->nx;
+    c->dy = c->dim == 2 ? (d->y1 - d->y0) / (double)c->ny : 1.0;
+    c->area_const = c->dim == 2 ? c->dx * c->dy : c->dx;
+    // Delta = 2 |Omega| / P: dx in 1D, dx dy / (dx + dy) for a rectangle
+    c->min_delta = c->dim == 2 ? 2.0 * c->dx * c->dy / (2.0 * c->dx + 2.0 * c->dy) : c->dx;
+    for (int i = 0; i < 4; ++i) c->bc[i] = d->bc[i];
+    c->stream = (cudaStream_t)stream;
+    if (d->bathymetry) c->bed_host.assign(d->bathymetry, d->bathymetry + c->nc);
+    zoomy_status st = ctx_init_device(c);
+    if (st != ZOOMY_OK) {
+        zoomy_mesh_destroy(c);
+        return st;
+    }
+    *out = c;
+    return ZOOMY_OK;
+}
+
+zoomy_status zoomy::ctx_init_device(zoomy_ctx *c)
+{
+    ZCHECK(cudaGetDevice(&c->device));
+    ZCHECK(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device));
+    ZCHECK(cudaMalloc(&c->ctl, sizeof(DevCtl)));
+    ZCHECK(cudaMalloc(&c->ctl_aux, sizeof(DevCtl)));
+    ZCHECK(cudaMalloc(&c->partials, sizeof(double) * (NPARTIAL + 1)));
+    ZCHECK(cudaMemsetAsync(c->ctl, 0, sizeof(DevCtl), c->stream));
+    ZCHECK(cudaStreamSynchronize(c->stream));
+    return ZOOMY_OK;
+}
+
+extern "C" zoomy_status zoomy_mesh_destroy(zoomy_ctx *c)
+{
+    if (!c) return ZOOMY_OK;
+    if (c->stream || c->ctl) cudaStreamSynchronize(c->stream);
+    cudaFree(c->ctl);
+    cudaFree(c->ctl_aux);
+    cudaFree(c->partials);
+    cudaFree(c->bed_dev);
+    cudaFree(c->q1);
+    cudaFree(c->qdev_host);
+    for (cudaEvent_t ev : c->prof_events) cudaEventDestroy(ev);
+    tri_free(c);
+    delete c;
+    return ZOOMY_OK;
+}
+
+extern "C" zoomy_status zoomy_set_stream(zoomy_ctx *c, void *stream)
+{
+    if (!c) return set_error(ZOOMY_EINVAL, "zoomy_set_stream: NULL context");
+    c->stream = (cudaStream_t)stream;
+    return ZOOMY_OK;
+}
+
+extern "C" zoomy_status zoomy_mesh_info(zoomy_ctx *c, int64_t *ncells, double *min_delta)
+{
+    if (!c) return set_error(ZOOMY_EINVAL, "zoomy_mesh_info: NULL context");
+    if (ncells) *ncells = c->nc;
+    if (min_delta) *min_delta = c->min_delta;
+    return ZOOMY_OK;
+}
+
+extern "C" zoomy_status zoomy_mesh_permutation(zoomy_ctx *c, int64_t *perm)
+{
+    if (!c || !perm) return set_error(ZOOMY_EINVAL, "zoomy_mesh_permutation: NULL argument");
+    if (c->kind == ZOOMY_MESH_TRI && !c->perm.empty()) {
+        memcpy(perm, c->perm.data(), sizeof(int64_t) * c->nc);
+    } else {
+        for (int64_t i = 0; i < c->nc; ++i) perm[i] = i;
+    }
+    return ZOOMY_OK;
+}
+
+extern "C" zoomy_status zoomy_model_set(zoomy_ctx *c, int32_t level, const zoomy_friction *fr, double g, double cfl,
+                                        double h_dry, int32_t dtype)
+{
+    if (!c) return set_error(ZOOMY_EINVAL, "zoomy_model_set: NULL context");
+    if (level < 0 || level > ZOOMY_MAX_LEVEL)
+        return set_error(ZOOMY_EINVAL, "zoomy_model_set: level %d outside [0, %d]", level, ZOOMY_MAX_LEVEL);
+    if (!(g > 0.0) || !(cfl > 0.0 && cfl <= 1.0) || !(h_dry >= 0.0))
+        return set_error(ZOOMY_EINVAL, "zoomy_model_set: need g > 0, 0 < cfl <= 1, h_dry >= 0");
+    if (dtype != ZOOMY_FP32 && dtype != ZOOMY_FP64) return set_error(ZOOMY_EINVAL, "zoomy_model_set: bad dtype");
+    zoomy_friction f = {ZOOMY_FRICTION_NONE, 0.0, 0.0, 1.0, 0.0};
+    if (fr) f = *fr;
+    if (f.kind < 0 || f.kind > 2 || !(f.rho > 0.0) || f.C < 0.0 || f.nu < 0.0 || f.manning_n < 0.0)
+        return set_error(ZOOMY_EINVAL, "zoomy_model_set: bad friction parameters");
+    if (c->kind == ZOOMY_MESH_TRI && dtype != ZOOMY_FP32)
+        return set_error(ZOOMY_EINVAL, "zoomy_model_set: triangle meshes run the FP32 state path");
+    c->level = level;
+    c->fric = f;
+    c->g = g;
+    c->cfl = cfl;
+    c->hdry = h_dry;
+    c->nv = c->dim == 1 ? level + 2 : 2 * level + 3;
+    if (c->dtype != dtype || !c->bed_dev) {
+        cudaFree(c->bed_dev);
+        c->bed_dev = nullptr;
+        c->dtype = dtype;
+        if (!c->bed_host.empty()) {
+            size_t es = elem_size(dtype);
+            ZCHECK(cudaMalloc(&c->bed_dev, es * c->nc));
+            std::vector<char> tmp(es * c->nc);
+            for (int64_t i = 0; i < c->nc; ++i) {
+                double b = c->bed_host[c->kind == ZOOMY_MESH_TRI && !c->perm.empty() ? c->perm[i] : i];
+                if (dtype == ZOOMY_FP64)
+                    ((double *)tmp.data())[i] = b;
+                else
+                    ((float *)tmp.data())[i] = (float)b;
+            }
+            ZCHECK(cudaMemcpyAsync(c->bed_dev, tmp.data(), es * c->nc, cudaMemcpyHostToDevice, c->stream));
+            ZCHECK(cudaStreamSynchronize(c->stream));
+        }
+    }
+    c->model_ok = true;
+    return ZOOMY_OK;
+}
+
+extern "C" zoomy_status zoomy_nvars(zoomy_ctx *c, int32_t *nv)
+{
+    if (!c || !nv) return set_error(ZOOMY_EINVAL, "zoomy_nvars: NULL argument");
+    if (!c->model_ok) return set_error(ZOOMY_ESTATE, "zoomy_nvars: call zoomy_model_set first");
+    *nv = c->nv;
+    return ZOOMY_OK;
+}
+
+static zoomy_status ensure_stage_buffer(zoomy_ctx *c, int64_t ld)
+{
+    size_t need = elem_size(c->dtype) * (size_t)c->nv * (size_t)ld;
+    if (c->q1 && c->q1_bytes >= need) return ZOOMY_OK;
+    cudaFree(c->q1);
+    c->q1 = nullptr;
+    c->q1_bytes = 0;
+    ZCHECK(cudaMalloc(&c->q1, need));
+    c->q1_bytes = need;
+    return ZOOMY_OK;
+}
+
+template <typename T>
+static void fill_args(zoomy_ctx *c, StageArgs<T> &a, int64_t ld, double dt)
+{
+    memset(&a, 0, sizeof(a));
+    a.bed = (const T *)c->bed_dev;
+    a.ld = ld;
+    a.nx = (int)c->nx;
+    a.ny = (int)c->ny;
+    a.inv_dx = T(1.0 / c->dx);
+    a.inv_dy = T(1.0 / c->dy);
+    for (int i = 0; i < 4; ++i) a.bc[i] = c->bc[i];
+    a.g = T(c->g);
+    a.hdry = T(c->hdry);
+    a.fric = c->fric.kind;
+    a.nu_rho = c->fric.kind == ZOOMY_FRICTION_SLIP_NEWTONIAN ? T(c->fric.nu / c->fric.rho) : T(0);
+    a.C_rho = T(c->fric.C / c->fric.rho);
+    a.gn2 = T(c->g * c->fric.manning_n * c->fric.manning_n);
+    a.cfl = c->cfl;
+    a.dmin = c->min_delta;
+    a.dt_fixed = dt;
+    a.ctl = c->ctl;
+    a.H = c->rows_per_warp;
+    a.nstrips = (int)((c->nx + 29) / 30);
+    a.nsegs = (int)((c->ny + a.H - 1) / a.H);
+}
+
+template <typename T>
+static zoomy_status run_steps(zoomy_ctx *c, T *Q, int64_t ld, double dt, int nsteps)
+{
+    T *Q1 = (T *)c->q1;
+    if (dt <= 0.0) {
+        cudaError_t e = launch_wavespeed<T>(c->dim, c->level, Q, ld, c->nc, T(c->g), T(c->hdry), c->ctl, 0, c->nsm,
+                                            c->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "wavespeed launch");
+    }
+    if (c->kind == ZOOMY_MESH_TRI) return tri_run_steps(c, (float *)Q, ld, dt, nsteps);
+    StageArgs<T> a;
+    fill_args<T>(c, a, ld, dt);
+    for (int s = 0; s < nsteps; ++s) {
+        a.slot_in = s & 1;
+        a.slot_out = (s + 1) & 1;
+        a.X = Q;
+        a.Qn = Q;
+        a.out = Q1;
+        zoomy_status ps = prof_mark(c, 1, true);
+        if (ps != ZOOMY_OK) return ps;
+        cudaError_t e = launch_stage_struct<T>(c->dim, c->level, a, 1, c->warps_per_block, c->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "stage 1 launch");
+        if ((ps = prof_mark(c, 1, false)) != ZOOMY_OK) return ps;
+        a.X = Q1;
+        a.Qn = Q;
+        a.out = Q;
+        if ((ps = prof_mark(c, 2, true)) != ZOOMY_OK) return ps;
+        e = launch_stage_struct<T>(c->dim, c->level, a, 2, c->warps_per_block, c->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "stage 2 launch");
+        if ((ps = prof_mark(c, 2, false)) != ZOOMY_OK) return ps;
+    }
+    return ZOOMY_OK;
+}
+
+zoomy_status zoomy::read_status(zoomy_ctx *c, double *t_total)
+{
+    DevCtl h;
+    ZCHECK(cudaMemcpyAsync(&h, c->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream));
+    ZCHECK(cudaStreamSynchronize(c->stream));
+    // the time and the sticky status are consumed by this read
+    ZCHECK(cudaMemsetAsync((char *)c->ctl + offsetof(DevCtl, t), 0, sizeof(DevCtl) - offsetof(DevCtl, t), c->stream));
+    if (t_total) *t_total = h.t;
+    if (h.status & DEV_NAN) return set_error(ZOOMY_ENAN, "a step produced a non-finite state");
+    if (h.status & DEV_NEGDEPTH) return set_error(ZOOMY_ENEGDEPTH, "a step produced a negative depth");
+    if (h.status & DEV_NOWAVE) return set_error(ZOOMY_ECFL, "no positive finite wave speed for the CFL step");
+    return ZOOMY_OK;
+}
+
+zoomy_status zoomy::check_step_args(zoomy_ctx *c, const void *Q, int64_t ld, double dt, int32_t nsteps,
+                                    const char *who)
+{
+    if (!c) return set_error(ZOOMY_EINVAL, "%s: NULL context", who);
+    if (!c->model_ok) return set_error(ZOOMY_ESTATE, "%s: call zoomy_model_set first", who);
+    if (!Q) return set_error(ZOOMY_EINVAL, "%s: NULL state", who);
+    if (ld < c->nc) return set_error(ZOOMY_EINVAL, "%s: ld = %lld < ncells = %lld", who, (long long)ld, (long long)c->nc);
+    if (((uintptr_t)Q) % elem_size(c->dtype)) return set_error(ZOOMY_EINVAL, "%s: misaligned state pointer", who);
+    if (nsteps < 0) return set_error(ZOOMY_EINVAL, "%s: nsteps < 0", who);
+    if (!(dt >= 0.0) || dt > 1e300) return set_error(ZOOMY_EINVAL, "%s: dt must be >= 0 and finite", who);
+    return ZOOMY_OK;
+}
+
+extern "C" zoomy_status zoomy_step(zoomy_ctx *c, void *Q, int64_t ld, double dt, int32_t nsteps, double *t_advanced)
+{
+    zoomy_status st = check_step_args(c, Q, ld, dt, nsteps, "zoomy_step");
+    if (st != ZOOMY_OK) return st;
+    st = ensure_stage_buffer(c, ld);
+    if (st != ZOOMY_OK) return st;
+    // reset the wave-speed slots; time and status accumulate until read (read_status)
+    ZCHECK(cudaMemsetAsync(c->ctl, 0, offsetof(DevCtl, t), c->stream));
+    st = c->dtype == ZOOMY_FP64 ? run_steps<double>(c, (double *)Q, ld, dt, nsteps)
+                                : run_steps<float>(c, (float *)Q, ld, dt, nsteps);
+    if (st != ZOOMY_OK) return st;
+    if (t_advanced) return read_status(c, t_advanced);
+    return ZOOMY_OK;
+}
+
+extern "C" zoomy_status zoomy_step_host(zoomy_ctx *c, void *Qh, int64_t ld, double dt, int32_t nsteps,
+                                        double *t_advanced)
+{
+    zoomy_status st = check_step_args(c, Qh, ld, dt, nsteps, "zoomy_step_host");
+    if (st != ZOOMY_OK) return st;
+    size_t bytes = elem_size(c->dtype) * (size_t)c->nv * (size_t)ld;
+    if (!c->qdev_host || c->qdev_host_bytes < bytes) {
+        cudaFree(c->qdev_host);
+        c->qdev_host = nullptr;
+        ZCHECK(cudaMalloc(&c->qdev_host, bytes));
+        c->qdev_host_bytes = bytes;
+    }
+    ZCHECK(cudaMemcpyAsync(c->qdev_host, Qh, bytes, cudaMemcpyHostToDevice, c->stream));
+    double t = 0.0;
+    st = zoomy_step(c, c->qdev_host, ld, dt, nsteps, nullptr);
+    if (st != ZOOMY_OK) return st;
+    ZCHECK(cudaMemcpyAsync(Qh, c->qdev_host, bytes, cudaMemcpyDeviceToHost, c->stream));
+    st = read_status(c, &t);
+    if (t_advanced) *t_advanced = t;
+    return st;
+}
+
+extern "C" zoomy_status zoomy_sync(zoomy_ctx *c, double *t_total)
+{
+    if (!c) return set_error(ZOOMY_EINVAL, "zoomy_sync: NULL context");
+    return read_status(c, t_total);
+}
+
+extern "C" zoomy_status zoomy_max_wavespeed(zoomy_ctx *c, const void *Q, int64_t ld, double *out)
+{
+    zoomy_status st = check_step_args(c, Q, ld, 0.0, 0, "zoomy_max_wavespeed");
+    if (st != ZOOMY_OK) return st;
+    if (!out) return set_error(ZOOMY_EINVAL, "zoomy_max_wavespeed: NULL output");
+    ZCHECK(cudaMemsetAsync(c->ctl_aux, 0, sizeof(DevCtl), c->stream));
+    cudaError_t e = c->dtype == ZOOMY_FP64
+                        ? launch_wavespeed<double>(c->dim, c->level, (const double *)Q, ld, c->nc, c->g, c->hdry,
+                                                   c->ctl_aux, 0, c->nsm, c->stream)
+                        : launch_wavespeed<float>(c->dim, c->level, (const float *)Q, ld, c->nc, (float)c->g,
+                                                  (float)c->hdry, c->ctl_aux, 0, c->nsm, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "wavespeed launch");
+    DevCtl h;
+    ZCHECK(cudaMemcpyAsync(&h, c->ctl_aux, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream));
+    ZCHECK(cudaStreamSynchronize(c->stream));
+    if (c->dtype == ZOOMY_FP64) {
+        double v;
+        memcpy(&v, &h.smax_d[0], 8);
+        *out = v;
+    } else {
+        float v;
+        memcpy(&v, &h.smax_f[0], 4);
+        *out = v;
+    }
+    if (h.status & DEV_NAN) return set_error(ZOOMY_ENAN, "non-finite state");
+    return ZOOMY_OK;
+}
+
+extern "C" zoomy_status zoomy_mass(zoomy_ctx *c, const void *Q, int64_t ld, double *out)
+{
+    zoomy_status st = check_step_args(c, Q, ld, 0.0, 0, "zoomy_mass");
+    if (st != ZOOMY_OK) return st;
+    if (!out) return set_error(ZOOMY_EINVAL, "zoomy_mass: NULL output");
+    const double *area = c->kind == ZOOMY_MESH_TRI ? c->tri_area_d : nullptr;
+    cudaError_t e = c->dtype == ZOOMY_FP64
+                        ? launch_mass<double>((const double *)Q, c->nc, c->area_const, area, c->partials, NPARTIAL,
+                                              c->partials + NPARTIAL, c->stream)
+                        : launch_mass<float>((const float *)Q, c->nc, c->area_const, area, c->partials, NPARTIAL,
+                                             c->partials + NPARTIAL, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mass launch");
+    ZCHECK(cudaMemcpyAsync(out, c->partials + NPARTIAL, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    ZCHECK(cudaStreamSynchronize(c->stream));
+    return ZOOMY_OK;
+}
+
+extern "C" zoomy_status zoomy_tune_set(zoomy_ctx *c, int32_t rows_per_warp, int32_t warps_per_block)
+{
+    if (!c) return set_error(ZOOMY_EINVAL, "zoomy_tune_set: NULL context");
+    if (rows_per_warp < 1 || rows_per_warp > 4096 || warps_per_block < 1 || warps_per_block > 32)
+        return set_error(ZOOMY_EINVAL, "zoomy_tune_set: rows_per_warp in [1, 4096], warps_per_block in [1, 32]");
+    c->rows_per_warp = rows_per_warp;
+    c->warps_per_block = warps_per_block;
+    return ZOOMY_OK;
+}
+
+zoomy_status zoomy::prof_mark(zoomy_ctx *c, int stage, bool start)
+{
+    if (!c->prof_on) return ZOOMY_OK;
+    if (c->prof_used == c->prof_events.size()) {
+        cudaEvent_t ev;
+        ZCHECK(cudaEventCreate(&ev));
+        c->prof_events.push_back(ev);
+    }
+    if (start) c->prof_kind.push_back(stage);
+    ZCHECK(cudaEventRecord(c->prof_events[c->prof_used++], c->stream));
+    return ZOOMY_OK;
+}
+
+extern "C" zoomy_status zoomy_profile_enable(zoomy_ctx *c, int32_t on)
+{
+    if (!c) return set_error(ZOOMY_EINVAL, "zoomy_profile_enable: NULL context");
+    c->prof_on = on != 0;
+    c->prof_used = 0;
+    c->prof_kind.clear();
+    return ZOOMY_OK;
+}
+
+extern "C" zoomy_status zoomy_profile_read(zoomy_ctx *c, int64_t *launches, double *total_ms)
+{
+    if (!c || !launches || !total_ms) return set_error(ZOOMY_EINVAL, "zoomy_profile_read: NULL argument");
+    ZCHECK(cudaStreamSynchronize(c->stream));
+    launches[0] = launches[1] = 0;
+    total_ms[0] = total_ms[1] = 0.0;
+    for (size_t k = 0; k < c->prof_kind.size(); ++k) {
+        float ms = 0.f;
+        ZCHECK(cudaEventElapsedTime(&ms, c->prof_events[2 * k], c->prof_events[2 * k + 1]));
+        int s = c->prof_kind[k] - 1;
+        launches[s] += 1;
+        total_ms[s] += ms;
+    }
+    c->prof_used = 0;
+    c->prof_kind.clear();
+    return ZOOMY_OK;
+}

@@ -1,0 +1,67 @@
+// zoomy_internal.h -- the context object behind the opaque zoomy_ctx handle (internal).
+#pragma once
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/zoomy.h"
+
+#define ZOOMY_MAX_LEVEL 4
+
+namespace zoomy {
+struct DevCtl;
+constexpr int NPARTIAL = 1024;  // blocks of the fixed-order FP64 mass sum
+}  // namespace zoomy
+
+struct zoomy_ctx {
+    // mesh
+    int kind = 0, dim = 1;
+    int64_t nx = 0, ny = 1, nc = 0;
+    double dx = 1, dy = 1, area_const = 1, min_delta = 1;
+    int bc[4] = {0, 0, 0, 0};
+    std::vector<double> bed_host;   // caller's cell order
+    std::vector<int64_t> perm;      // triangles: perm[new] = caller index
+    // device / stream
+    cudaStream_t stream = nullptr;
+    int device = 0, nsm = 1;
+    // model
+    bool model_ok = false;
+    int level = 0, dtype = 0, nv = 0;
+    zoomy_friction fric = {0, 0.0, 0.0, 1.0, 0.0};
+    double g = 9.81, cfl = 0.45, hdry = 0.0;
+    // device buffers owned by the context
+    void *bed_dev = nullptr;
+    void *q1 = nullptr;
+    size_t q1_bytes = 0;
+    void *qdev_host = nullptr;      // device copy used by zoomy_step_host
+    size_t qdev_host_bytes = 0;
+    zoomy::DevCtl *ctl = nullptr;      // step control: wave-speed slots, time, sticky status
+    zoomy::DevCtl *ctl_aux = nullptr;  // scratch of the synchronous reductions
+    double *partials = nullptr;
+    // structured 2D decomposition (rows per warp segment, warps per block)
+    int rows_per_warp = 64, warps_per_block = 4;
+    // stage-kernel profiling (zoomy_profile_enable)
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_events;  // pool, reused
+    std::vector<int> prof_kind;            // stage of each recorded (start, stop) pair
+    size_t prof_used = 0;                  // events in use
+    // triangle mesh (device)
+    int32_t *tri_nbr_d = nullptr;   // [3][nc] neighbour cell or -1
+    float *tri_geo_d = nullptr;     // per cell-face normals and lengths / area
+    double *tri_area_d = nullptr;   // [nc]
+};
+
+namespace zoomy {
+zoomy_status set_error(zoomy_status st, const char *fmt, ...);
+zoomy_status cuda_fail(cudaError_t e, const char *where);
+zoomy_status ctx_init_device(zoomy_ctx *c);
+zoomy_status read_status(zoomy_ctx *c, double *t_total);
+// record a profiling event before / after a stage launch (no-op when profiling is off)
+zoomy_status prof_mark(zoomy_ctx *c, int stage, bool start);
+zoomy_status check_step_args(zoomy_ctx *c, const void *Q, int64_t ld, double dt, int32_t nsteps, const char *who);
+// triangle meshes (fv_tri.cu)
+zoomy_status create_tri_mesh(const zoomy_mesh_desc *d, void *stream, zoomy_ctx **out);
+void tri_free(zoomy_ctx *c);
+zoomy_status tri_run_steps(zoomy_ctx *c, float *Q, int64_t ld, double dt, int nsteps);
+}  // namespace zoomy
