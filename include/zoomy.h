@@ -148,6 +148,15 @@ zoomy_status zoomy_mass(zoomy_ctx *ctx, const void *Q, int64_t ld, double *out);
  * per CTA.  rows_per_warp in [1, 4096], warps_per_block in [1, 32]. */
 zoomy_status zoomy_tune_set(zoomy_ctx *ctx, int32_t rows_per_warp, int32_t warps_per_block);
 
+/* Autotuner of the structured 2D decomposition: times both stage kernels on the state Q (device,
+ * left unchanged; a temporary copy is used for the in-place stage) for each candidate rows_per_warp
+ * (and warps_per_block where the kernel has that freedom) and keeps the fastest pair in the context.
+ * cache_path (may be NULL): a JSON-lines file; an entry for the same (grid, level, dtype, device)
+ * is reused without measuring, a new measurement is appended.  *rows_per_warp_out and
+ * *us_per_step_out (may be NULL) receive the choice and its measured stage-1 + stage-2 time. */
+zoomy_status zoomy_autotune(zoomy_ctx *ctx, const void *Q, int64_t ld, const char *cache_path,
+                            int32_t *rows_per_warp_out, double *us_per_step_out);
+
 /* Per-launch timing of the stage kernels with CUDA events recorded on the context's stream
  * around every stage launch (on = 1) or off (on = 0, default).  zoomy_profile_read waits for
  * the stream and returns the launch counts and the summed device time in milliseconds of the

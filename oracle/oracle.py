@@ -85,6 +85,8 @@ def _declare(L):
     L.or_stage.argtypes = [vp, vp, _dp, vp, C.c_double, _dp]
     L.or_step.argtypes = [vp, vp, _dp, vp, C.c_double, C.c_double, C.c_int,
                           C.POINTER(C.c_double)]
+    L.or_step_ex.argtypes = [vp, vp, _dp, vp, C.c_double, C.c_double, C.c_int, C.c_int,
+                             C.POINTER(C.c_double)]
     L.or_max_wavespeed.argtypes = [vp, vp, _dp]
     L.or_max_wavespeed.restype = C.c_double
     L.or_min_delta.argtypes = [vp]
@@ -220,12 +222,15 @@ def stage(model, mesh, X, dt, bed=None):
     return Y
 
 
-def step(model, mesh, Q, nsteps, dt=0.0, cfl=0.45, bed=None):
-    """nsteps SSP-RK2 steps (dt > 0 fixed, dt <= 0 adaptive CFL). Returns (Q_new, t_advanced)."""
+def step(model, mesh, Q, nsteps, dt=0.0, cfl=0.45, bed=None, store_f32=False):
+    """nsteps SSP-RK2 steps (dt > 0 fixed, dt <= 0 adaptive CFL). Returns (Q_new, t_advanced).
+
+    store_f32 keeps the state in single precision between stages (FP64 arithmetic on it), the
+    precision form of an FP32-state implementation."""
     Q = np.array(Q, dtype=np.float64, order="C")
     b, bp = _bed_ptr(bed)
     t = C.c_double(0.0)
-    lib().or_step(model._p, mesh._p, Q, bp, dt, cfl, nsteps, C.byref(t))
+    lib().or_step_ex(model._p, mesh._p, Q, bp, dt, cfl, nsteps, 1 if store_f32 else 0, C.byref(t))
     return Q, t.value
 
 

@@ -651,11 +651,19 @@ double or_cfl_dt(const or_model *md, const or_mesh *me, const double *Q, double 
     return cfl * or_min_delta(me) / or_max_wavespeed(md, me, Q);
 }
 
+/* Precision form of the FP32 state: the state is kept in single precision between stages while
+ * every operation on it is FP64.  store_f32 != 0 rounds Q1 and Q^{n+1} to the nearest float at
+ * the points where an FP32-state implementation stores them. */
+static void round_to_float(double *a, int64_t n)
+{
+    for (int64_t k = 0; k < n; ++k) a[k] = (double)(float)a[k];
+}
+
 /* nsteps SSP-RK2 steps: Q1 = stage(Qn), Q2 = stage(Q1), Qn+1 = (Qn + Q2)/2.
  * dt_fixed > 0 uses that step; dt_fixed <= 0 recomputes dt from Qn every step.
  * Q is [nv][nc]; bed may be NULL (flat).  Returns the time advanced in *t_out. */
-int or_step(const or_model *md, const or_mesh *me, double *Q, const double *bed, double dt_fixed,
-            double cfl, int nsteps, double *t_out)
+int or_step_ex(const or_model *md, const or_mesh *me, double *Q, const double *bed, double dt_fixed,
+               double cfl, int nsteps, int store_f32, double *t_out)
 {
     int64_t n = (int64_t)md->nv * me->nc;
     double *Q1 = (double *)malloc(sizeof(double) * n);
@@ -664,14 +672,22 @@ int or_step(const or_model *md, const or_mesh *me, double *Q, const double *bed,
     for (int s = 0; s < nsteps; ++s) {
         double dt = dt_fixed > 0.0 ? dt_fixed : or_cfl_dt(md, me, Q, cfl);
         or_stage(md, me, Q, bed, dt, Q1);
+        if (store_f32) round_to_float(Q1, n);
         or_stage(md, me, Q1, bed, dt, Q2);
         for (int64_t k = 0; k < n; ++k) Q[k] = 0.5 * (Q[k] + Q2[k]);
+        if (store_f32) round_to_float(Q, n);
         t += dt;
     }
     free(Q1);
     free(Q2);
     if (t_out) *t_out = t;
     return 0;
+}
+
+int or_step(const or_model *md, const or_mesh *me, double *Q, const double *bed, double dt_fixed,
+            double cfl, int nsteps, double *t_out)
+{
+    return or_step_ex(md, me, Q, bed, dt_fixed, cfl, nsteps, 0, t_out);
 }
 
 /* Total mass sum_i |Omega_i| h_i (FP64). */

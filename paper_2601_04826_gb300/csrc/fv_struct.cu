@@ -154,6 +154,15 @@ __global__ void __launch_bounds__(128) k_stage_2d(StageArgs<T> a)
 
     CellRec<N, 2, T> prev, cur;
     T xprev[nv], xcur[nv], accp[nv], accc[nv];
+    // loop-carried values start defined (the first row is a halo row whose faces are unused)
+    {
+        T zero[m];
+#pragma unroll
+        for (int k = 0; k < m; ++k) zero[k] = T(0);
+        make_cell<N, 2, T>(prev, T(0), T(0), zero, zero, a.hdry);
+#pragma unroll
+        for (int v = 0; v < nv; ++v) xprev[v] = accp[v] = T(0);
+    }
     T smax = T(0);
     unsigned int flag = 0;
 

@@ -40,26 +40,42 @@ __device__ __forceinline__ T dev_sqrt(T a)
 }
 
 // Hydrostatic reconstruction depth h* = max(0, h + b - bf) (Audusse et al.), the bed/surface
-// difference the method needs in FP64 precision.  In FP32 the sum h + (b - bf) is formed
-// without rounding error by two error-free additions (Knuth's TwoSum) and rounded once, which
-// is what an FP64 evaluation followed by a cast gives up to a double-rounding tie.  On the
-// higher side (b == bf) h* = h exactly.
-__device__ __forceinline__ float hr_depth(float h, float b, float bf)
+// difference the method needs in FP64 precision.  In FP32 it is returned as an unevaluated pair
+// hi + lo equal to h + b - bf up to about 2^-46 relative: the sum is formed by two error-free
+// additions (Knuth's TwoSum), so the face differences hR* - hL* that drive the pressure and mass
+// terms keep the accuracy of an FP64 evaluation even where they are far below the FP32
+// resolution of h.  On the higher side (b == bf) h* = h exactly.
+struct HPair {
+    float hi, lo;
+};
+__device__ __forceinline__ HPair hr_depth(float h, float b, float bf)
 {
-    if (b >= bf) return fmaxf(h, 0.0f);
+    if (b >= bf) return {fmaxf(h, 0.0f), 0.0f};
     float s = b - bf;
     float bb = s - b;
     float e = (b - (s - bb)) + (-bf - bb);
     float r = h + s;
     float bb2 = r - h;
     float e2 = (h - (r - bb2)) + (s - bb2);
-    return fmaxf(r + (e2 + e), 0.0f);
+    float lo = e2 + e;
+    float hi = r + lo;             // rounded depth
+    lo = lo - (hi - r);            // remainder, |lo| <= ulp(hi)/2 (Fast2Sum, |r| >= |lo|)
+    if (hi <= 0.0f) return {0.0f, 0.0f};
+    return {hi, lo};
 }
-__device__ __forceinline__ double hr_depth(double h, double b, double bf)
+__device__ __forceinline__ float hp_diff(HPair r, HPair l) { return (r.hi - l.hi) + (r.lo - l.lo); }
+__device__ __forceinline__ float hp_val(HPair a) { return a.hi; }
+
+struct DPair {
+    double hi;
+};
+__device__ __forceinline__ DPair hr_depth(double h, double b, double bf)
 {
     double hs = (h + b) - bf;
-    return hs > 0.0 ? hs : 0.0;
+    return {hs > 0.0 ? hs : 0.0};
 }
+__device__ __forceinline__ double hp_diff(DPair r, DPair l) { return r.hi - l.hi; }
+__device__ __forceinline__ double hp_val(DPair a) { return a.hi; }
 
 // One cell, primitive form, with the per-unit-depth flux products it contributes to faces.
 template <int N, int D, typename T>
@@ -164,8 +180,10 @@ __device__ __forceinline__ void face_term(const CellRec<N, D, T> &L, const Frame
 {
     constexpr int m = N + 1;
     const T bf = L.b > R.b ? L.b : R.b;
-    const T hl = hr_depth(L.h, L.b, bf);
-    const T hr = hr_depth(R.h, R.b, bf);
+    const auto hpl = hr_depth(L.h, L.b, bf);
+    const auto hpr = hr_depth(R.h, R.b, bf);
+    const T hl = hp_val(hpl), hr = hp_val(hpr);
+    const T dh = hp_diff(hpr, hpl);  // hR* - hL* with the bed/surface difference kept exact
     const bool wl = hl > hdry, wr = hr > hdry;
     // wave speeds of the reconstructed states
     const T sl = wl ? L.um + dev_sqrt(g * hl + L.s2) + L.s1 : dev_sqrt(g * hl);
@@ -181,20 +199,19 @@ __device__ __forceinline__ void face_term(const CellRec<N, D, T> &L, const Frame
 #pragma unroll
         for (int k = 0; k < m; ++k) dt_[k] = er * FR.t[k] - el * FL.t[k];
     }
-    fc[0] = T(0.5) * (el * FL.n[0] + er * FR.n[0]) - hs * (hr - hl);
+    fc[0] = T(0.5) * (el * FL.n[0] + er * FR.n[0]) - hs * dh;
 #pragma unroll
     for (int k = 0; k < m; ++k) fc[1 + k] = T(0.5) * (el * FL.gnn[k] + er * FR.gnn[k]) - hs * dn[k];
     if constexpr (D == 2) {
 #pragma unroll
         for (int k = 0; k < m; ++k) fc[1 + m + k] = T(0.5) * (el * FL.gnt[k] + er * FR.gnt[k]) - hs * dt_[k];
     }
-    pd = T(0.25) * g * (hr - hl) * (hr + hl);
+    pd = T(0.25) * g * dh * (hr + hl);
 
 #pragma unroll
     for (int k = 0; k < 1 + (D == 2 ? 2 : 1) * m; ++k) nc[k] = T(0);
     if constexpr (N >= 1) {
         // path-averaged velocity moments along Psi(s) = QL* + s dQ (3-point Gauss-Legendre)
-        const T dh = hr - hl;
         T nbar[m], tbar[D == 2 ? m : 1];
 #pragma unroll
         for (int k = 0; k < m; ++k) nbar[k] = T(0);

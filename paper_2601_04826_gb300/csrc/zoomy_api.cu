@@ -4,6 +4,8 @@
 #include <cstdarg>
 #include <cstddef>
 #include <cstdio>
+#include <cstdlib>
+#include <string>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -169,12 +171,14 @@ extern "C" zoomy_status zoomy_model_set(zoomy_ctx *c, int32_t level, const zoomy
         cudaFree(c->bed_dev);
         c->bed_dev = nullptr;
         c->dtype = dtype;
-        if (!c->bed_host.empty()) {
+        // a flat bed is stored as zeros so that the kernels read one layout
+        {
             size_t es = elem_size(dtype);
             ZCHECK(cudaMalloc(&c->bed_dev, es * c->nc));
             std::vector<char> tmp(es * c->nc);
             for (int64_t i = 0; i < c->nc; ++i) {
-                double b = c->bed_host[c->kind == ZOOMY_MESH_TRI && !c->perm.empty() ? c->perm[i] : i];
+                double b = c->bed_host.empty() ? 0.0
+                                               : c->bed_host[c->kind == ZOOMY_MESH_TRI && !c->perm.empty() ? c->perm[i] : i];
                 if (dtype == ZOOMY_FP64)
                     ((double *)tmp.data())[i] = b;
                 else
@@ -235,6 +239,17 @@ static void fill_args(zoomy_ctx *c, StageArgs<T> &a, int64_t ld, double dt)
 }
 
 template <typename T>
+static cudaError_t launch_stage(zoomy_ctx *c, const StageArgs<T> &a, int stage)
+{
+    if constexpr (sizeof(T) == 4) {
+        // the specialised FP32 kernel indexes with 32-bit offsets
+        if (c->dim == 2 && (int64_t)c->nv * a.ld < (1LL << 31))
+            return launch_stage_2d_f32(c->level, a, stage, c->warps_per_block, c->stream);
+    }
+    return launch_stage_struct<T>(c->dim, c->level, a, stage, c->warps_per_block, c->stream);
+}
+
+template <typename T>
 static zoomy_status run_steps(zoomy_ctx *c, T *Q, int64_t ld, double dt, int nsteps)
 {
     T *Q1 = (T *)c->q1;
@@ -254,14 +269,14 @@ static zoomy_status run_steps(zoomy_ctx *c, T *Q, int64_t ld, double dt, int nst
         a.out = Q1;
         zoomy_status ps = prof_mark(c, 1, true);
         if (ps != ZOOMY_OK) return ps;
-        cudaError_t e = launch_stage_struct<T>(c->dim, c->level, a, 1, c->warps_per_block, c->stream);
+        cudaError_t e = launch_stage<T>(c, a, 1);
         if (e != cudaSuccess) return cuda_fail(e, "stage 1 launch");
         if ((ps = prof_mark(c, 1, false)) != ZOOMY_OK) return ps;
         a.X = Q1;
         a.Qn = Q;
         a.out = Q;
         if ((ps = prof_mark(c, 2, true)) != ZOOMY_OK) return ps;
-        e = launch_stage_struct<T>(c->dim, c->level, a, 2, c->warps_per_block, c->stream);
+        e = launch_stage<T>(c, a, 2);
         if (e != cudaSuccess) return cuda_fail(e, "stage 2 launch");
         if ((ps = prof_mark(c, 2, false)) != ZOOMY_OK) return ps;
     }
@@ -430,5 +445,146 @@ extern "C" zoomy_status zoomy_profile_read(zoomy_ctx *c, int64_t *launches, doub
     }
     c->prof_used = 0;
     c->prof_kind.clear();
+    return ZOOMY_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Autotuner (structured 2D): rows per warp segment and warps per block
+// ------------------------------------------------------------------------------------------
+
+static std::string tune_key(zoomy_ctx *c)
+{
+    char buf[256];
+    cudaDeviceProp p;
+    cudaGetDeviceProperties(&p, c->device);
+    snprintf(buf, sizeof(buf), "%s|sm%d|%lldx%lld|L%d|%s", p.name, p.multiProcessorCount, (long long)c->nx,
+             (long long)c->ny, c->level, c->dtype == ZOOMY_FP64 ? "f64" : "f32");
+    return buf;
+}
+
+static bool tune_cache_lookup(const char *path, const std::string &key, int *H, int *W, double *us)
+{
+    if (!path) return false;
+    FILE *f = fopen(path, "r");
+    if (!f) return false;
+    char line[512];
+    bool found = false;
+    while (fgets(line, sizeof(line), f)) {
+        const char *k = strstr(line, "\"key\": \"");
+        if (!k) continue;
+        k += 8;
+        const char *e = strchr(k, '"');
+        if (!e || std::string(k, e - k) != key) continue;
+        const char *h = strstr(line, "\"rows_per_warp\": ");
+        const char *w = strstr(line, "\"warps_per_block\": ");
+        const char *u = strstr(line, "\"us_per_step\": ");
+        if (h && w) {
+            *H = atoi(h + 17);
+            *W = atoi(w + 19);
+            *us = u ? atof(u + 15) : 0.0;
+            found = *H >= 1 && *W >= 1;
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+template <typename T>
+static zoomy_status tune_measure(zoomy_ctx *c, const T *Q, int64_t ld, int H, int W, T *tmp, double *us)
+{
+    StageArgs<T> a;
+    int saveH = c->rows_per_warp, saveW = c->warps_per_block;
+    c->rows_per_warp = H;
+    c->warps_per_block = W;
+    fill_args<T>(c, a, ld, 1e-9);  // a tiny fixed step: the timing does not depend on it
+    a.slot_in = 0;
+    a.slot_out = 1;
+    cudaEvent_t e0, e1;
+    ZCHECK(cudaEventCreate(&e0));
+    ZCHECK(cudaEventCreate(&e1));
+    const int reps = 4;
+    float best = 1e30f;
+    for (int rep = 0; rep < reps + 1; ++rep) {
+        ZCHECK(cudaEventRecord(e0, c->stream));
+        a.X = Q;
+        a.Qn = Q;
+        a.out = (T *)c->q1;
+        cudaError_t e = launch_stage<T>(c, a, 1);
+        if (e != cudaSuccess) return cuda_fail(e, "autotune stage 1");
+        a.X = (const T *)c->q1;
+        a.Qn = tmp;
+        a.out = tmp;
+        e = launch_stage<T>(c, a, 2);
+        if (e != cudaSuccess) return cuda_fail(e, "autotune stage 2");
+        ZCHECK(cudaEventRecord(e1, c->stream));
+        ZCHECK(cudaEventSynchronize(e1));
+        float ms;
+        ZCHECK(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0 && ms < best) best = ms;  // the first repetition warms up
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->rows_per_warp = saveH;
+    c->warps_per_block = saveW;
+    *us = best * 1e3;
+    return ZOOMY_OK;
+}
+
+extern "C" zoomy_status zoomy_autotune(zoomy_ctx *c, const void *Q, int64_t ld, const char *cache_path,
+                                       int32_t *rows_per_warp_out, double *us_per_step_out)
+{
+    zoomy_status st = check_step_args(c, Q, ld, 0.0, 0, "zoomy_autotune");
+    if (st != ZOOMY_OK) return st;
+    if (c->kind != ZOOMY_MESH_2D) {  // only the structured 2D kernels have a decomposition to tune
+        if (rows_per_warp_out) *rows_per_warp_out = c->rows_per_warp;
+        if (us_per_step_out) *us_per_step_out = 0.0;
+        return ZOOMY_OK;
+    }
+    const std::string key = tune_key(c);
+    int H = 0, W = 0;
+    double us = 0.0;
+    if (!tune_cache_lookup(cache_path, key, &H, &W, &us)) {
+        if ((st = ensure_stage_buffer(c, ld)) != ZOOMY_OK) return st;
+        size_t bytes = elem_size(c->dtype) * (size_t)c->nv * (size_t)ld;
+        void *tmp = nullptr;
+        ZCHECK(cudaMalloc(&tmp, bytes));
+        ZCHECK(cudaMemcpyAsync(tmp, Q, bytes, cudaMemcpyDeviceToDevice, c->stream));
+        const int Hs[] = {8, 12, 16, 20, 24, 32, 40, 48, 56, 64, 72, 80, 96, 112, 128, 160, 192, 256};
+        const int Ws_generic[] = {1, 2, 4};
+        const bool packed = c->dtype == ZOOMY_FP32 && (int64_t)c->nv * ld < (1LL << 31);
+        double best = 1e300;
+        for (int h : Hs) {
+            if (h > c->ny && h != Hs[0]) continue;
+            for (int w : Ws_generic) {
+                if (packed && w != 1) continue;  // the FP32 kernel runs one warp per CTA
+                double t;
+                st = c->dtype == ZOOMY_FP64 ? tune_measure<double>(c, (const double *)Q, ld, h, w, (double *)tmp, &t)
+                                            : tune_measure<float>(c, (const float *)Q, ld, h, w, (float *)tmp, &t);
+                if (st != ZOOMY_OK) {
+                    cudaFree(tmp);
+                    return st;
+                }
+                if (t < best) {
+                    best = t;
+                    H = h;
+                    W = w;
+                }
+            }
+        }
+        cudaFree(tmp);
+        us = best;
+        if (cache_path) {
+            FILE *f = fopen(cache_path, "a");
+            if (f) {
+                fprintf(f, "{\"key\": \"%s\", \"rows_per_warp\": %d, \"warps_per_block\": %d, \"us_per_step\": %.3f}\n",
+                        key.c_str(), H, W, us);
+                fclose(f);
+            }
+        }
+    }
+    c->rows_per_warp = H;
+    c->warps_per_block = W;
+    if (rows_per_warp_out) *rows_per_warp_out = H;
+    if (us_per_step_out) *us_per_step_out = us;
     return ZOOMY_OK;
 }

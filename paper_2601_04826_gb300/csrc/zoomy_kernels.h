@@ -13,6 +13,9 @@ template <typename T>
 cudaError_t launch_stage_struct(int dim, int level, const StageArgs<T> &a, int stage, int warps_per_block,
                                 cudaStream_t st);
 
+cudaError_t launch_stage_2d_f32(int level, const StageArgs<float> &a, int stage, int warps_per_block,
+                                cudaStream_t st);
+
 template <typename T>
 cudaError_t launch_wavespeed(int dim, int level, const T *Q, int64_t ld, int64_t nc, T g, T hdry, DevCtl *ctl,
                              int slot, int nsm, cudaStream_t st);

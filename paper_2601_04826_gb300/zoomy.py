@@ -61,6 +61,8 @@ _SIGNATURES = [
     ("zoomy_max_wavespeed", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_double)]),
     ("zoomy_mass", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_double)]),
     ("zoomy_tune_set", C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
+    ("zoomy_autotune", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_char_p, C.POINTER(C.c_int32),
+                                 C.POINTER(C.c_double)]),
     ("zoomy_profile_enable", C.c_int, [C.c_void_p, C.c_int32]),
     ("zoomy_profile_read", C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     ("zoomy_last_error", C.c_char_p, []),
@@ -188,6 +190,14 @@ def zoomy_tune_set(ctx, rows_per_warp, warps_per_block):
     _check(lib().zoomy_tune_set(ctx, rows_per_warp, warps_per_block))
 
 
+def zoomy_autotune(ctx, Q, ld, cache_path=None):
+    h = C.c_int32()
+    us = C.c_double()
+    _check(lib().zoomy_autotune(ctx, _ptr(Q), ld, cache_path.encode() if cache_path else None, C.byref(h),
+                                C.byref(us)))
+    return h.value, us.value
+
+
 def zoomy_profile_enable(ctx, on=True):
     _check(lib().zoomy_profile_enable(ctx, 1 if on else 0))
 
@@ -293,6 +303,9 @@ class Context:
 
     def tune(self, rows_per_warp, warps_per_block):
         zoomy_tune_set(self.ctx, rows_per_warp, warps_per_block)
+
+    def autotune(self, Q, cache_path=None):
+        return zoomy_autotune(self.ctx, Q, self._ld(Q), cache_path)
 
     def permutation(self):
         import numpy as np
