@@ -100,31 +100,34 @@ __device__ __forceinline__ void make_side(Side2<N> &r, float h, float b, const f
     });
 }
 
-// Hydrostatic depths of one face (scalar, branch-free): hl, hr and hR* - hL* with the
-// FP64-grade bed/surface difference (exact pair of model.cuh's hr_depth).
-__device__ __forceinline__ void hr_face(float hL, float bL, float hR, float bR, float &hl, float &hr, float &dh,
-                                        bool &lowL)
+// Hydrostatic depths of both faces (branch-free): hl, hr and hR* - hL*, with the FP64-grade
+// bed/surface difference: h + (b - bf) of the lower side is formed by two TwoSums (the exact pair of
+// model.cuh's hr_depth), evaluated for the x- and the y-face at once with packed additions.
+__device__ __forceinline__ void hr_faces(F2 hL, F2 bL, float hR, float bR, F2 &hl, F2 &hr, F2 &dh, bool &lowLx,
+                                         bool &lowLy)
 {
-    lowL = bL < bR;
-    const float bf = fmaxf(bL, bR);
-    const float h = lowL ? hL : hR, b = lowL ? bL : bR;
-    // h + (b - bf) by two TwoSums; exact (h, 0) when b == bf
-    const float s = b - bf;
-    const float bb = s - b;
-    const float e = (b - (s - bb)) + (-bf - bb);
-    const float r = h + s;
-    const float bb2 = r - h;
-    const float e2 = (h - (r - bb2)) + (s - bb2);
-    float lo = e2 + e;
-    float hi = r + lo;
+    lowLx = bL.x() < bR;
+    lowLy = bL.y() < bR;
+    const F2 bf(fmaxf(bL.x(), bR), fmaxf(bL.y(), bR));
+    const F2 h(lowLx ? hL.x() : hR, lowLy ? hL.y() : hR);
+    const F2 b(lowLx ? bL.x() : bR, lowLy ? bL.y() : bR);
+    const F2 s = b - bf;
+    const F2 bb = s - b;
+    const F2 e = (b - (s - bb)) - (bf + bb);
+    const F2 r = h + s;
+    const F2 bb2 = r - h;
+    const F2 e2 = (h - (r - bb2)) + (s - bb2);
+    F2 lo = e2 + e;
+    F2 hi = r + lo;
     lo = lo - (hi - r);
-    const bool pos = hi > 0.0f;
-    hi = pos ? hi : 0.0f;
-    lo = pos ? lo : 0.0f;
-    const float hh = fmaxf(lowL ? hR : hL, 0.0f);  // the higher side keeps its depth
-    hl = lowL ? hi : hh;
-    hr = lowL ? hh : hi;
-    dh = lowL ? (hr - hl) - lo : (hr - hl) + lo;
+    const bool px = hi.x() > 0.0f, py = hi.y() > 0.0f;
+    hi = F2(px ? hi.x() : 0.0f, py ? hi.y() : 0.0f);
+    lo = F2(px ? lo.x() : 0.0f, py ? lo.y() : 0.0f);
+    const F2 hh(fmaxf(lowLx ? hR : hL.x(), 0.0f), fmaxf(lowLy ? hR : hL.y(), 0.0f));  // higher side
+    hl = F2(lowLx ? hi.x() : hh.x(), lowLy ? hi.y() : hh.y());
+    hr = F2(lowLx ? hh.x() : hi.x(), lowLy ? hh.y() : hi.y());
+    const F2 sl(lowLx ? -lo.x() : lo.x(), lowLy ? -lo.y() : lo.y());
+    dh = (hr - hl) + sl;
 }
 
 // Face terms for the pair of faces (formulas of face_term in model.cuh), returned as
@@ -139,11 +142,10 @@ __device__ __forceinline__ void face2(const F2 *Ln, const F2 *Lt, const F2 *Lgnn
                                       float g, float hdry, F2 scale, F2 *pr, F2 *mi)
 {
     constexpr int m = N + 1;
-    float hlx, hrx, dhx, hly, hry, dhy;
+    F2 hl, hr, dh;
     bool lowLx, lowLy;
-    hr_face(Ln[m].x(), Lt[m].x(), R.h, R.b, hlx, hrx, dhx, lowLx);
-    hr_face(Ln[m].y(), Lt[m].y(), R.h, R.b, hly, hry, dhy, lowLy);
-    const F2 hl(hlx, hly), hr(hrx, hry), dh(dhx, dhy);
+    hr_faces(Ln[m], Lt[m], R.h, R.b, hl, hr, dh, lowLx, lowLy);
+    const float hlx = hl.x(), hly = hl.y(), hrx = hr.x(), hry = hr.y();
     // wave speed of the lower side at its reconstructed depth; the higher side keeps its own
     auto lower_speed = [&](float hs, float um, float s2, float s1) {
         const bool w = hs > hdry;
@@ -156,10 +158,11 @@ __device__ __forceinline__ void face2(const F2 *Ln, const F2 *Lt, const F2 *Lgnn
                                     lowLy ? Ln[m + 1].y() : R.s1);
     const float slx = lowLx ? slowx : Lt[m + 1].x(), srx = lowLx ? R.sc : slowx;
     const float sly = lowLy ? slowy : Lt[m + 1].y(), sry = lowLy ? R.sc : slowy;
-    const F2 hs = F2(0.5f) * F2(fmaxf(slx, srx), fmaxf(sly, sry));
+    // every face term is multiplied by scale = dt |e| / |Omega|: fold it into the constants
+    const F2 half = F2(0.5f) * scale;
+    const F2 hs = half * F2(fmaxf(slx, srx), fmaxf(sly, sry));
     const F2 el(hlx > hdry ? hlx : 0.0f, hly > hdry ? hly : 0.0f);
     const F2 er(hrx > hdry ? hrx : 0.0f, hry > hdry ? hry : 0.0f);
-    const F2 half(0.5f);
     F2 qln[m], qlt[m], dn[m], dtv[m];
 #pragma unroll
     for (int k = 0; k < m; ++k) {
@@ -175,7 +178,7 @@ __device__ __forceinline__ void face2(const F2 *Ln, const F2 *Lt, const F2 *Lgnn
         fc[1 + k] = half * fma2(el, Lgnn[k], er * R.gnn[k]) - hs * dn[k];
         fc[1 + m + k] = half * fma2(el, Lgnt[k], er * R.gnt[k]) - hs * dtv[k];
     }
-    const F2 pd = F2(0.25f * g) * dh * (hr + hl);
+    const F2 pd = (F2(0.25f * g) * scale) * dh * (hr + hl);
     F2 nc[1 + 2 * m];
     if constexpr (N >= 1) {
         // sum_q w_q (QL* + s_q dQ)/h(s_q) = QL* W0 + dQ W1 (wet nodes only), 3-point Gauss-Legendre
@@ -218,20 +221,19 @@ __device__ __forceinline__ void face2(const F2 *Ln, const F2 *Lt, const F2 *Lgnn
             nc[1 + m + k] = half * rt;
         });
     }
-    const F2 pds = pd * scale;
 #pragma unroll
     for (int k = 0; k < 1 + 2 * m; ++k) {
         const bool has_nc = (N >= 1) && ((k >= 2 && k <= m) || k >= m + 2);
         if (has_nc) {
-            pr[k] = (fc[k] - nc[k]) * scale;
-            mi[k] = (fc[k] + nc[k]) * scale;
+            pr[k] = fc[k] - nc[k];
+            mi[k] = fc[k] + nc[k];
         } else {
-            pr[k] = fc[k] * scale;
-            mi[k] = pr[k];
+            pr[k] = fc[k];
+            mi[k] = fc[k];
         }
     }
-    pr[1] = pr[1] - pds;
-    mi[1] = mi[1] + pds;
+    pr[1] = pr[1] - pd;
+    mi[1] = mi[1] + pd;
 }
 
 // Bottom stress (implicit, rank-1 Sherman-Morrison) and dry cut, branch-free (see
@@ -330,6 +332,11 @@ __device__ __forceinline__ void row_body(const StageArgs<float> &a, const RowCtx
         const float *p = a.Qn + ((fin ? r - 1 : r0) * c.nx + c.csrc);
 #pragma unroll
         for (int v = 0; v < nv; ++v) qn[v] = p[v * c.ld];
+        if (xrow) {  // bring Q^n of this row into L2; it is read when the row is finished
+            const float *pn = a.Qn + (r * c.nx + c.csrc);
+#pragma unroll
+            for (int v = 0; v < nv; ++v) asm volatile("prefetch.global.L2 [%0];" ::"l"(pn + v * c.ld));
+        }
     }
     // ---- left neighbour (x-face) from the lane on the left, lower neighbour (y-face) from P ----
     // Ln/Lt/Lgnn/Lgnt carry the face-frame pairs; index m / m+1 carry (h, b), (um, s2), (s1, sc).
