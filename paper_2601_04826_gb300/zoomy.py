@@ -65,6 +65,10 @@ _SIGNATURES = [
                                  C.POINTER(C.c_double)]),
     ("zoomy_profile_enable", C.c_int, [C.c_void_p, C.c_int32]),
     ("zoomy_profile_read", C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
+    ("zoomy_step_noalloc", C.c_int, [C.c_int64, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_double,
+                                     C.POINTER(C.c_int32), C.c_int32, C.POINTER(zoomy_friction), C.c_double,
+                                     C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_int64, C.c_double,
+                                     C.c_int32, C.c_void_p, C.POINTER(C.c_double)]),
     ("zoomy_last_error", C.c_char_p, []),
 ]
 
@@ -207,6 +211,17 @@ def zoomy_profile_read(ctx):
     ms = (C.c_double * 2)()
     _check(lib().zoomy_profile_read(ctx, n, ms))
     return list(n), list(ms)
+
+
+def zoomy_step_noalloc(nx, ny, x0, x1, y0, y1, bc, level, friction, g, cfl, h_dry, bed, Q, ld, dt, nsteps,
+                       stream=None, sync=True):
+    """The allocation-free step (see include/zoomy.h): every argument is passed through unchanged."""
+    bcs = (C.c_int32 * 4)(*bc)
+    t = C.c_double()
+    _check(lib().zoomy_step_noalloc(nx, ny, x0, x1, y0, y1, bcs, level,
+                                    C.byref(friction) if friction is not None else None, g, cfl, h_dry, _ptr(bed),
+                                    _ptr(Q), ld, dt, nsteps, _stream(stream), C.byref(t) if sync else None))
+    return t.value if sync else None
 
 
 def zoomy_last_error():
