@@ -148,8 +148,12 @@ def run_ours(args, rank, world, local_rank):
     ctx = zoomy.Context(zoomy.mesh_2d(N_SIDE, N_SIDE, bathymetry=b), LEVEL, fr, cfl=CFL, dtype=zoomy.FP32)
     Q = torch.tensor(Q0, dtype=torch.float32, device=dev)
 
-    # launch configuration from the autotuner, then warm-up
-    tuned_rows, tuned_us = ctx.autotune(Q)
+    # launch configuration from the autotuner (or given, for profiling runs), then warm-up
+    if args.rows_per_warp:
+        zoomy.zoomy_tune_set(ctx.ctx, args.rows_per_warp, 1)
+        tuned_rows = args.rows_per_warp
+    else:
+        tuned_rows, _ = ctx.autotune(Q)
     ctx.step(Q, nsteps=args.warmup, dt=0.0)
 
     def barrier():
@@ -314,6 +318,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    ap.add_argument("--rows-per-warp", type=int, default=0,
+                    help="fixed structured-kernel segment height instead of the autotuner (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
