@@ -35,7 +35,8 @@ CFL = 0.45
 # stage 2 reads Q1 (7) + b + Q^n (7), writes Q^{n+1} (7)
 BYTES_STAGE = {1: 4 * (NV + 1 + NV), 2: 4 * (NV + 1 + NV + NV)}
 METRIC = "cell-updates/sec and % of HBM peak per FV step"
-KERNEL_SOURCES = ["paper_2601_04826_gb300/csrc/fv_struct2d_f32.cu", "paper_2601_04826_gb300/csrc/f32x2.cuh",
+KERNEL_SOURCES = ["paper_2601_04826_gb300/csrc/fv_struct2d_f32.cu", "paper_2601_04826_gb300/csrc/struct2d_f32.cuh",
+                  "paper_2601_04826_gb300/csrc/f32x2.cuh",
                   "paper_2601_04826_gb300/csrc/model.cuh", "paper_2601_04826_gb300/csrc/fv_common.cuh",
                   "paper_2601_04826_gb300/csrc/basis.cuh"]
 
@@ -291,6 +292,47 @@ def run_tri(args):
             "gpu_launches": int(launches[0] + launches[1] + 1), "clocks": clk.summary()}
 
 
+def run_ensemble(args):
+    """Config-4 workload: 512 independent level-1 members, sides ~ U{64..512}, slip ~ logNormal(-2, 0.5),
+    one persistent launch per call captured in a CUDA graph.  Prints its own JSON line."""
+    import torch
+
+    from paper_2601_04826_gb300 import build, inputs, zoomy
+
+    build.build()
+    level, nv = 1, 5
+    sides, slip, seeds = inputs.ensemble_members(512, seed=0)
+    Q0, offs = inputs.ensemble_state(sides, seeds, level)
+    nc = int(offs[-1])
+    ens = zoomy.zoomy_ensemble_create(sides, slip, level)
+    Q = torch.tensor(Q0, dtype=torch.float32, device="cuda")
+    rows, _ = zoomy.zoomy_ensemble_autotune(ens, Q, nc)
+    zoomy.zoomy_ensemble_step(ens, Q, nc, args.warmup, mode=0)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        zoomy.zoomy_ensemble_step(ens, Q, nc, args.steps, mode=0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    zoomy.zoomy_mesh_destroy(ens)
+    hbm, peak_kind = peaks()
+    step_bytes = 4 * ((nv + 1 + nv) + (3 * nv + 1)) * nc  # both stages, bed included
+    achieved = step_bytes * args.steps / (ms * 1e-3) / 1e9
+    return {"metric": METRIC, "value": nc * args.steps / (ms * 1e-3), "unit": "cell-updates/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Gaussian bumps)",
+            "config": {"workload": f"batched ensemble: 512 level-1 members, sides U{{64..512}} ({nc} cells), "
+                                   "slip logNormal(-2, 0.5), walls, one persistent cooperative launch per call in "
+                                   "a CUDA graph", "rows_per_warp": rows},
+            "roofline": {"bound": "hbm", "kernel": "k_ensemble_persistent<1>", "achieved": achieved, "peak": hbm,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                         "note": "whole persistent launch (both stages and barriers) over its duration"},
+            "gpu_launches": 1, "clocks": clk.summary()}
+
+
 def oracle_window_run(side, nsteps):
     """The oracle on a side x side window of the workload (cells of the 2048^2 grid, walls)."""
     import numpy as np
@@ -367,8 +409,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
-    ap.add_argument("--workload", choices=["grid", "tri"], default="grid",
-                    help="grid: the 2048^2 level-2 benchmark (default); tri: the ~4M-triangle level-3 dam break")
+    ap.add_argument("--workload", choices=["grid", "tri", "ensemble"], default="grid",
+                    help="grid: the 2048^2 level-2 benchmark (default); tri: the ~4M-triangle level-3 dam break; "
+                         "ensemble: 512 ragged level-1 members in one persistent launch")
     ap.add_argument("--rows-per-warp", type=int, default=0,
                     help="fixed structured-kernel segment height instead of the autotuner (profiling runs)")
     args = ap.parse_args()
@@ -386,6 +429,8 @@ def main():
         line = run_reference(args, rank, world)
     elif args.workload == "tri":
         line = run_tri(args) if rank == 0 else None
+    elif args.workload == "ensemble":
+        line = run_ensemble(args) if rank == 0 else None
     else:
         line = run_ours(args, rank, world, local_rank)
     if rank == 0 and line is not None:

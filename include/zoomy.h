@@ -157,6 +157,38 @@ zoomy_status zoomy_tune_set(zoomy_ctx *ctx, int32_t rows_per_warp, int32_t warps
 zoomy_status zoomy_autotune(zoomy_ctx *ctx, const void *Q, int64_t ld, const char *cache_path,
                             int32_t *rows_per_warp_out, double *us_per_step_out);
 
+/* ---- Batched ensembles (independent runs of uneven sizes in one launch) -------------------------
+ * nmembers square grids of side sides[m] on the unit square with walls, each with its own slip
+ * coefficient C[m] (Navier slip, rho = 1) and the Newtonian viscosity nu, level `level`, FP32
+ * state, its own CFL step (cfl, g, h_dry as in zoomy_model_set).  The members' states are
+ * concatenated: member m's cell (i, j) is at offsets[m] + j sides[m] + i of each variable plane of
+ * one SoA array Q[v][ld], ld >= offsets[nmembers] (zoomy_ensemble_offsets). */
+zoomy_status zoomy_ensemble_create(int32_t nmembers, const int64_t *sides, const double *C, int32_t level,
+                                   double nu, double g, double cfl, double h_dry, void *stream, zoomy_ctx **out);
+
+/* offsets[0..nmembers] (host): start of each member in the concatenated state, and the total. */
+zoomy_status zoomy_ensemble_offsets(zoomy_ctx *ctx, int64_t *offsets);
+
+/* Advance every member by nsteps SSP-RK2 steps with its own CFL step.  mode 0: one persistent
+ * cooperative launch (grid-wide barriers between phases, dynamic work distribution over
+ * (member, strip, row segment) items) captured in a CUDA graph; mode 1: the same launch without the
+ * graph; mode 2: one launch per phase (2 nsteps + 1) captured in a CUDA graph; mode 3: those launches
+ * without the graph.  All modes give bitwise the same result.  Synchronises; t_members (host,
+ * nmembers, may be NULL) receives each member's simulated time.  A barrier wait that exceeds its
+ * spin limit makes the kernel return and the call report ZOOMY_ETIMEOUT. */
+zoomy_status zoomy_ensemble_step(zoomy_ctx *ctx, void *Q, int64_t ld, int32_t nsteps, int32_t mode,
+                                 double *t_members);
+
+/* Pick the row-segment height of the ensemble's work items by timing two persistent steps per
+ * candidate on a scratch copy of Q (Q is left unchanged). */
+zoomy_status zoomy_ensemble_autotune(zoomy_ctx *ctx, void *Q, int64_t ld, int32_t *rows_per_warp_out,
+                                     double *us_per_step_out);
+
+/* Barrier settings of the persistent ensemble kernel: spin_limit bounds every wait (iterations of a
+ * ~64 ns sleep; default 2e7); extra_participants > 0 makes every barrier wait for participants that
+ * never arrive, which exercises the timeout path (testing). */
+zoomy_status zoomy_ensemble_set_barrier(zoomy_ctx *ctx, int64_t spin_limit, int32_t extra_participants);
+
 /* Per-launch timing of the stage kernels with CUDA events recorded on the context's stream
  * around every stage launch (on = 1) or off (on = 0, default).  zoomy_profile_read waits for
  * the stream and returns the launch counts and the summed device time in milliseconds of the

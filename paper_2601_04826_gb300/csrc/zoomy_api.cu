@@ -116,6 +116,7 @@ extern "C" zoomy_status zoomy_mesh_destroy(zoomy_ctx *c)
     cudaFree(c->qdev_host);
     for (cudaEvent_t ev : c->prof_events) cudaEventDestroy(ev);
     tri_free(c);
+    ens_free(c);
     delete c;
     return ZOOMY_OK;
 }
@@ -314,6 +315,7 @@ extern "C" zoomy_status zoomy_step(zoomy_ctx *c, void *Q, int64_t ld, double dt,
 {
     zoomy_status st = check_step_args(c, Q, ld, dt, nsteps, "zoomy_step");
     if (st != ZOOMY_OK) return st;
+    if (c->kind == ZOOMY_MESH_ENSEMBLE) return set_error(ZOOMY_EINVAL, "zoomy_step: use zoomy_ensemble_step");
     st = ensure_stage_buffer(c, ld);
     if (st != ZOOMY_OK) return st;
     // reset the wave-speed slots; time and status accumulate until read (read_status)

@@ -8,6 +8,7 @@
 #include "../../include/zoomy.h"
 
 #define ZOOMY_MAX_LEVEL 4
+#define ZOOMY_MESH_ENSEMBLE 3  // internal kind of an ensemble context (zoomy_ensemble_create)
 
 namespace zoomy {
 struct DevCtl;
@@ -46,6 +47,8 @@ struct zoomy_ctx {
     std::vector<cudaEvent_t> prof_events;  // pool, reused
     std::vector<int> prof_kind;            // stage of each recorded (start, stop) pair
     size_t prof_used = 0;                  // events in use
+    // ensemble (fv_ensemble.cu)
+    void *ens = nullptr;
     // triangle mesh (device)
     int32_t *tri_nbr_d = nullptr;   // [3][nc] neighbour cell or -1
     float *tri_geo_d = nullptr;     // per cell-face normals and lengths / area
@@ -63,5 +66,6 @@ zoomy_status check_step_args(zoomy_ctx *c, const void *Q, int64_t ld, double dt,
 // triangle meshes (fv_tri.cu)
 zoomy_status create_tri_mesh(const zoomy_mesh_desc *d, void *stream, zoomy_ctx **out);
 void tri_free(zoomy_ctx *c);
+void ens_free(zoomy_ctx *c);
 zoomy_status tri_run_steps(zoomy_ctx *c, float *Q, int64_t ld, double dt, int nsteps);
 }  // namespace zoomy

@@ -186,3 +186,15 @@ def ensemble_members(n_members=512, seed=0, side_lo=64, side_hi=512, mu=-2.0, si
     lam = rng.lognormal(mu, sigma, size=n_members)
     seeds = rng.integers(0, 2**31 - 1, size=n_members)
     return sides, lam, seeds
+
+
+def ensemble_state(sides, seeds, level, amp_range=(0.1, 0.5), sigma=0.05):
+    """Concatenated initial states of square members: base depth 1, flat bed, at rest, with a
+    seeded Gaussian bump per member.  Returns (Q [nv, sum side^2], offsets [nmembers + 1])."""
+    offs = np.concatenate([[0], np.cumsum(np.asarray(sides, dtype=np.int64) ** 2)])
+    Q = np.zeros((nvars(level, 2), offs[-1]))
+    for m, (s, sd) in enumerate(zip(sides, seeds)):
+        Qm, _ = gaussian_bump_2d(int(s), int(s), level, seed=int(sd), bathymetry=False, amp_range=amp_range,
+                                 sigma=sigma)
+        Q[:, offs[m]:offs[m + 1]] = Qm
+    return Q, offs

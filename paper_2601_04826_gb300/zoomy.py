@@ -63,6 +63,13 @@ _SIGNATURES = [
     ("zoomy_tune_set", C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
     ("zoomy_autotune", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_char_p, C.POINTER(C.c_int32),
                                  C.POINTER(C.c_double)]),
+    ("zoomy_ensemble_create", C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_double,
+                                        C.c_double, C.c_double, C.c_void_p, C.POINTER(C.c_void_p)]),
+    ("zoomy_ensemble_offsets", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("zoomy_ensemble_step", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p]),
+    ("zoomy_ensemble_autotune", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int32),
+                                          C.POINTER(C.c_double)]),
+    ("zoomy_ensemble_set_barrier", C.c_int, [C.c_void_p, C.c_int64, C.c_int32]),
     ("zoomy_profile_enable", C.c_int, [C.c_void_p, C.c_int32]),
     ("zoomy_profile_read", C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     ("zoomy_step_noalloc", C.c_int, [C.c_int64, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_double,
@@ -200,6 +207,44 @@ def zoomy_autotune(ctx, Q, ld, cache_path=None):
     _check(lib().zoomy_autotune(ctx, _ptr(Q), ld, cache_path.encode() if cache_path else None, C.byref(h),
                                 C.byref(us)))
     return h.value, us.value
+
+
+def zoomy_ensemble_create(sides, slip, level, nu=0.01, g=9.81, cfl=0.45, h_dry=1e-6, stream=None):
+    import numpy as np
+
+    sd = np.ascontiguousarray(sides, dtype=np.int64)
+    cc = np.ascontiguousarray(slip, dtype=np.float64)
+    h = C.c_void_p()
+    _check(lib().zoomy_ensemble_create(len(sd), sd.ctypes.data, cc.ctypes.data, level, nu, g, cfl, h_dry,
+                                       _stream(stream), C.byref(h)))
+    return h.value
+
+
+def zoomy_ensemble_offsets(ctx, nmembers):
+    import numpy as np
+
+    off = np.zeros(nmembers + 1, dtype=np.int64)
+    _check(lib().zoomy_ensemble_offsets(ctx, off.ctypes.data))
+    return off
+
+
+def zoomy_ensemble_step(ctx, Q, ld, nsteps, mode=0, nmembers=None):
+    import numpy as np
+
+    t = np.zeros(nmembers, dtype=np.float64) if nmembers else None
+    _check(lib().zoomy_ensemble_step(ctx, _ptr(Q), ld, nsteps, mode, t.ctypes.data if t is not None else None))
+    return t
+
+
+def zoomy_ensemble_autotune(ctx, Q, ld):
+    h = C.c_int32()
+    us = C.c_double()
+    _check(lib().zoomy_ensemble_autotune(ctx, _ptr(Q), ld, C.byref(h), C.byref(us)))
+    return h.value, us.value
+
+
+def zoomy_ensemble_set_barrier(ctx, spin_limit=20000000, extra_participants=0):
+    _check(lib().zoomy_ensemble_set_barrier(ctx, spin_limit, extra_participants))
 
 
 def zoomy_profile_enable(ctx, on=True):
