@@ -96,6 +96,14 @@ def _declare(L):
     L.or_mass.argtypes = [vp, _dp]
     L.or_mass.restype = C.c_double
     L.or_max_level.restype = C.c_int
+    L.or_closure_new.argtypes = [_dp, _dp, _dp, C.c_int]
+    L.or_closure_new.restype = vp
+    L.or_closure_free.argtypes = [vp]
+    L.or_closure_eval.argtypes = [vp, _dp, _dp]
+    L.or_closure_max_wavespeed.argtypes = [vp, vp, vp, _dp]
+    L.or_closure_max_wavespeed.restype = C.c_double
+    L.or_step_closure.argtypes = [vp, vp, vp, _dp, vp, C.c_double, C.c_double, C.c_int, C.c_int,
+                                  C.POINTER(C.c_double)]
 
 
 # --------------------------------------------------------------------------- basis
@@ -248,3 +256,41 @@ def mass(mesh, Q):
 
 def max_level():
     return lib().or_max_level()
+
+
+# --------------------------------------------------------------------------- learned closure
+
+class Closure:
+    """The closure MLP in the C oracle (params in the order of mlp.pack, FP64; bf16 mirrors the
+    inference kernel's BF16 layer inputs)."""
+
+    def __init__(self, params, in_scale, out_scale, bf16=True):
+        self._p = lib().or_closure_new(np.ascontiguousarray(params, dtype=np.float64),
+                                       np.ascontiguousarray(in_scale, dtype=np.float64),
+                                       np.ascontiguousarray(out_scale, dtype=np.float64), 1 if bf16 else 0)
+
+    def __del__(self):
+        if getattr(self, "_p", None):
+            lib().or_closure_free(self._p)
+            self._p = None
+
+    def eval(self, feat):
+        out = np.zeros(6)
+        lib().or_closure_eval(self._p, np.ascontiguousarray(feat, dtype=np.float64), out)
+        return out
+
+
+def step_closure(model4, closure, mesh, Q1, nsteps, dt=0.0, cfl=0.45, bed=None, store_f32=False):
+    """nsteps SSP-RK2 steps of the closure model (level-1 state [5, nc], level-4 model)."""
+    Q = np.array(Q1, dtype=np.float64, order="C")
+    b, bp = _bed_ptr(bed)
+    t = C.c_double(0.0)
+    rc = lib().or_step_closure(model4._p, closure._p, mesh._p, Q, bp, dt, cfl, nsteps, 1 if store_f32 else 0,
+                               C.byref(t))
+    if rc != 0:
+        raise ValueError("closure step needs a 2D level-4 model")
+    return Q, t.value
+
+
+def closure_max_wavespeed(model4, closure, mesh, Q1):
+    return lib().or_closure_max_wavespeed(model4._p, closure._p, mesh._p, np.ascontiguousarray(Q1, dtype=np.float64))

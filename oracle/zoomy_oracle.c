@@ -699,3 +699,220 @@ double or_mass(const or_mesh *me, const double *Q)
 }
 
 int or_max_level(void) { return OR_MAXN; }
+
+/* ------------------------------------------------------------------------- */
+/* Learned closure (level-1 prognostic state, level-4 model)                  */
+/* ------------------------------------------------------------------------- */
+/*
+ * Reading: the closure model is the level-4 system restricted to the rows of the level-1
+ * variables (h, hA_0, hB_0, hA_1, hB_1); the velocity moments alpha_k, beta_k of k = 2..4 come
+ * from a per-cell MLP of the level-1 state at every stage input (features h, u_m, v_m, alpha_1,
+ * beta_1, lambda scaled by in_scale; outputs scaled by out_scale).  Face terms are the level-4 ones
+ * on the closed states, projected on the level-1 rows; the Newtonian source sums over all five
+ * moments; the bottom stress is implicit in the two prognostic moments with the closed moments
+ * frozen at the stage input; the CFL speed is the level-4 bound on the closed state.
+ * GELU: tanh form.  bf16 != 0 rounds each layer input to BF16 (nearest, ties to even) like the
+ * tensor-core inference kernel; all arithmetic is FP64.
+ */
+typedef struct {
+    double W1[6 * 64], b1[64], W2[64 * 64], b2[64], W3[64 * 6], b3[6];
+    double in_scale[6], out_scale[6];
+    int bf16;
+} or_closure;
+
+or_closure *or_closure_new(const double *params, const double *in_scale, const double *out_scale, int bf16)
+{
+    or_closure *c = (or_closure *)calloc(1, sizeof(or_closure));
+    const double *p = params;
+    memcpy(c->W1, p, sizeof(c->W1)); p += 6 * 64;
+    memcpy(c->b1, p, sizeof(c->b1)); p += 64;
+    memcpy(c->W2, p, sizeof(c->W2)); p += 64 * 64;
+    memcpy(c->b2, p, sizeof(c->b2)); p += 64;
+    memcpy(c->W3, p, sizeof(c->W3)); p += 64 * 6;
+    memcpy(c->b3, p, sizeof(c->b3));
+    memcpy(c->in_scale, in_scale, sizeof(c->in_scale));
+    memcpy(c->out_scale, out_scale, sizeof(c->out_scale));
+    c->bf16 = bf16;
+    return c;
+}
+void or_closure_free(or_closure *c) { free(c); }
+
+static double round_bf16(double x)
+{
+    float f = (float)x;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    uint32_t lsb = (u >> 16) & 1u;
+    u = (u + 0x7fffu + lsb) & 0xffff0000u;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+static double gelu_tanh(double z)
+{
+    const double c = 0.79788456080286535588; /* sqrt(2/pi) */
+    return 0.5 * z * (1.0 + tanh(c * (z + 0.044715 * z * z * z)));
+}
+
+/* features (h, u_m, v_m, alpha_1, beta_1, lambda) -> (alpha_2, alpha_3, alpha_4, beta_2, beta_3, beta_4) */
+void or_closure_eval(const or_closure *c, const double *feat, double *out)
+{
+    double x[6], a1[64], a2[64];
+    for (int i = 0; i < 6; ++i) {
+        x[i] = feat[i] * c->in_scale[i];
+        if (c->bf16) x[i] = round_bf16(x[i]);
+    }
+    for (int j = 0; j < 64; ++j) {
+        double z = c->b1[j];
+        for (int i = 0; i < 6; ++i) z += x[i] * c->W1[i * 64 + j];
+        a1[j] = gelu_tanh(z);
+        if (c->bf16) a1[j] = round_bf16(a1[j]);
+    }
+    for (int j = 0; j < 64; ++j) {
+        double z = c->b2[j];
+        for (int i = 0; i < 64; ++i) z += a1[i] * c->W2[i * 64 + j];
+        a2[j] = gelu_tanh(z);
+        if (c->bf16) a2[j] = round_bf16(a2[j]);
+    }
+    for (int j = 0; j < 6; ++j) {
+        double z = c->b3[j];
+        for (int i = 0; i < 64; ++i) z += a2[i] * c->W3[i * 6 + j];
+        out[j] = z * c->out_scale[j];
+    }
+}
+
+/* The closed level-4 state of a level-1 state q1 (variables h, hA0, hB0, hA1, hB1); lambda is the
+ * slip feature.  Returns the closed velocity moments in alpha_hat / beta_hat (k = 2..4). */
+static void closure_embed(const or_model *m4, const or_closure *c, const double *q1, double lambda, double *q4,
+                          double *ahat, double *bhat)
+{
+    double h = q1[0];
+    double u = 0.0, v = 0.0, a1 = 0.0, b1 = 0.0;
+    if (h > m4->h_dry) {
+        u = q1[1] / h;
+        v = q1[2] / h;
+        a1 = q1[3] / h;
+        b1 = q1[4] / h;
+    }
+    double feat[6] = {h, u, v, a1, b1, lambda}, out[6];
+    or_closure_eval(c, feat, out);
+    for (int v2 = 0; v2 < m4->nv; ++v2) q4[v2] = 0.0;
+    q4[0] = h;
+    q4[ia(m4, 0)] = q1[1];
+    q4[ib(m4, 0)] = q1[2];
+    q4[ia(m4, 1)] = q1[3];
+    q4[ib(m4, 1)] = q1[4];
+    for (int k = 2; k <= 4; ++k) {
+        ahat[k] = h > m4->h_dry ? out[k - 2] : 0.0;
+        bhat[k] = h > m4->h_dry ? out[k + 1] : 0.0;
+        q4[ia(m4, k)] = h * ahat[k];
+        q4[ib(m4, k)] = h * bhat[k];
+    }
+}
+
+/* One closure stage Y = R(X + dt L(X)) on the level-1 state X [5][nc]. */
+static void closure_stage(const or_model *m4, const or_closure *cl, const or_mesh *me, const double *X,
+                          const double *bed, double dt, double *Y)
+{
+    int64_t nc = me->nc;
+    double *X4 = (double *)malloc(sizeof(double) * (size_t)m4->nv * nc);
+    double *sig = (double *)malloc(sizeof(double) * 2 * nc); /* sum_{k>=2} alpha_hat, beta_hat */
+    for (int64_t i = 0; i < nc; ++i) {
+        double q1[5], q4[OR_MAXV], ah[5], bh[5];
+        for (int v = 0; v < 5; ++v) q1[v] = X[(int64_t)v * nc + i];
+        closure_embed(m4, cl, q1, m4->C, q4, ah, bh);
+        for (int v = 0; v < m4->nv; ++v) X4[(int64_t)v * nc + i] = q4[v];
+        sig[2 * i] = ah[2] + ah[3] + ah[4];
+        sig[2 * i + 1] = bh[2] + bh[3] + bh[4];
+    }
+    const int rows[5] = {0, ia(m4, 0), ib(m4, 0), ia(m4, 1), ib(m4, 1)};
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < nc; ++i) {
+        double qi[OR_MAXV], qj[OR_MAXV], term[OR_MAXV], acc[OR_MAXV], S[OR_MAXV];
+        gather(X4, nc, m4->nv, i, qi);
+        double bi = bed ? bed[i] : 0.0;
+        for (int v = 0; v < m4->nv; ++v) acc[v] = 0.0;
+        for (int f = 0; f < me->nf; ++f) {
+            int64_t e = i * me->nf + f;
+            double nx = me->fnx[e], ny = me->fny[e], bj;
+            int64_t j = me->nbr[e];
+            if (j >= 0) {
+                gather(X4, nc, m4->nv, j, qj);
+                bj = bed ? bed[j] : 0.0;
+            } else {
+                ghost(m4, qi, me->fbc[e], nx, ny, qj);
+                bj = bi;
+            }
+            face_term(m4, qi, bi, qj, bj, nx, ny, term);
+            for (int v = 0; v < m4->nv; ++v) acc[v] += me->flen[e] * term[v];
+        }
+        or_source_newtonian(m4, qi, S);
+        double y[5];
+        for (int r = 0; r < 5; ++r) y[r] = X[(int64_t)r * nc + i] - dt / me->area[i] * acc[rows[r]] + dt * S[rows[r]];
+        /* bottom stress: implicit in the prognostic moments (rows 1..4), closed moments frozen */
+        double h = y[0];
+        if (!(h > m4->h_dry)) {
+            y[1] = y[2] = y[3] = y[4] = 0.0;
+        } else if (m4->fric != 0) {
+            double sa_hat = h * sig[2 * i], sb_hat = h * sig[2 * i + 1];
+            double c;
+            if (m4->fric == 1) {
+                c = m4->C / (m4->rho * h);
+            } else {
+                double ub = (y[1] + y[3] + sa_hat) / h, vb = (y[2] + y[4] + sb_hat) / h;
+                c = m4->g * m4->manning_n * m4->manning_n * sqrt(ub * ub + vb * vb) / pow(h, 4.0 / 3.0);
+            }
+            /* rows (hA0, hA1) with weights w = (1, 3): z + dt c w (z0 + z1) = y - dt c w sa_hat */
+            double ra0 = y[1] - dt * c * 1.0 * sa_hat, ra1 = y[3] - dt * c * 3.0 * sa_hat;
+            double rb0 = y[2] - dt * c * 1.0 * sb_hat, rb1 = y[4] - dt * c * 3.0 * sb_hat;
+            double den = 1.0 + dt * c * 4.0;
+            double fa = dt * c * (ra0 + ra1) / den, fb = dt * c * (rb0 + rb1) / den;
+            y[1] = ra0 - 1.0 * fa;
+            y[3] = ra1 - 3.0 * fa;
+            y[2] = rb0 - 1.0 * fb;
+            y[4] = rb1 - 3.0 * fb;
+        }
+        for (int r = 0; r < 5; ++r) Y[(int64_t)r * nc + i] = y[r];
+    }
+    free(X4);
+    free(sig);
+}
+
+/* Max level-4 wave speed of the closed state of Q1. */
+double or_closure_max_wavespeed(const or_model *m4, const or_closure *cl, const or_mesh *me, const double *Q1)
+{
+    double smax = 0.0;
+    for (int64_t i = 0; i < me->nc; ++i) {
+        double q1[5], q4[OR_MAXV], ah[5], bh[5];
+        for (int v = 0; v < 5; ++v) q1[v] = Q1[(int64_t)v * me->nc + i];
+        closure_embed(m4, cl, q1, m4->C, q4, ah, bh);
+        double s = or_wavespeed(m4, q4);
+        if (s > smax || s != s) smax = s;
+    }
+    return smax;
+}
+
+/* nsteps SSP-RK2 steps of the closure model on the level-1 state Q1 [5][nc]; m4 is the level-4 2D
+ * model (its C is the slip coefficient and the lambda feature).  store_f32 as in or_step_ex. */
+int or_step_closure(const or_model *m4, const or_closure *cl, const or_mesh *me, double *Q1, const double *bed,
+                    double dt_fixed, double cfl, int nsteps, int store_f32, double *t_out)
+{
+    if (m4->N != 4 || m4->dim != 2) return 1;
+    int64_t n = 5 * me->nc;
+    double *A = (double *)malloc(sizeof(double) * n);
+    double *B = (double *)malloc(sizeof(double) * n);
+    double t = 0.0;
+    for (int s = 0; s < nsteps; ++s) {
+        double dt = dt_fixed > 0.0 ? dt_fixed : cfl * or_min_delta(me) / or_closure_max_wavespeed(m4, cl, me, Q1);
+        closure_stage(m4, cl, me, Q1, bed, dt, A);
+        if (store_f32) round_to_float(A, n);
+        closure_stage(m4, cl, me, A, bed, dt, B);
+        for (int64_t k = 0; k < n; ++k) Q1[k] = 0.5 * (Q1[k] + B[k]);
+        if (store_f32) round_to_float(Q1, n);
+        t += dt;
+    }
+    free(A);
+    free(B);
+    if (t_out) *t_out = t;
+    return 0;
+}
