@@ -157,6 +157,26 @@ zoomy_status zoomy_tune_set(zoomy_ctx *ctx, int32_t rows_per_warp, int32_t warps
 zoomy_status zoomy_autotune(zoomy_ctx *ctx, const void *Q, int64_t ld, const char *cache_path,
                             int32_t *rows_per_warp_out, double *us_per_step_out);
 
+/* ---- Learned closure ---------------------------------------------------------------------------
+ * Turns a structured 2D level-1 FP32 context into the level-1 solver closed with learned level-4
+ * moments: the level-4 system restricted to the rows of (h, h alpha_0, h beta_0, h alpha_1,
+ * h beta_1), with alpha_2..4, beta_2..4 predicted per cell at every stage input by the MLP
+ *   x = (h, u_m, v_m, alpha_1, beta_1, lambda) * in_scale -> 64 -> 64 -> 6 (GELU, tanh form)
+ *   (alpha_2, alpha_3, alpha_4, beta_2, beta_3, beta_4) = y * out_scale
+ * run on the tensor cores inside the stage kernel (BF16 weights and layer inputs, FP32
+ * accumulation).  The paper's model hierarchy truncates the moments; the "material closure" it
+ * calls exchangeable is here a learned one.  params: 4998 host floats W1[6][64], b1[64],
+ * W2[64][64], b2[64], W3[64][6], b3[6] (weights rounded to BF16 on upload); lambda: the slip
+ * feature (normally the context's slip coefficient).  zoomy_step then advances the closed model;
+ * zoomy_closure_clear returns to the plain level-1 model. */
+zoomy_status zoomy_closure_set(zoomy_ctx *ctx, const float *params, const float *in_scale, const float *out_scale,
+                               double lambda);
+zoomy_status zoomy_closure_clear(zoomy_ctx *ctx);
+
+/* The closure MLP alone, with the in-kernel tensor-core code: feat (device, SoA [6][n], unscaled
+ * features) -> out (device, SoA [6][n], the six predicted moments).  Queued on the context's stream. */
+zoomy_status zoomy_closure_eval(zoomy_ctx *ctx, const float *feat, float *out, int64_t n);
+
 /* ---- Batched ensembles (independent runs of uneven sizes in one launch) -------------------------
  * nmembers square grids of side sides[m] on the unit square with walls, each with its own slip
  * coefficient C[m] (Navier slip, rho = 1) and the Newtonian viscosity nu, level `level`, FP32

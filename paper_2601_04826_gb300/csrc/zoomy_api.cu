@@ -114,6 +114,7 @@ extern "C" zoomy_status zoomy_mesh_destroy(zoomy_ctx *c)
     cudaFree(c->bed_dev);
     cudaFree(c->q1);
     cudaFree(c->qdev_host);
+    cudaFree(c->closure_d);
     for (cudaEvent_t ev : c->prof_events) cudaEventDestroy(ev);
     tri_free(c);
     ens_free(c);
@@ -253,6 +254,9 @@ static cudaError_t launch_stage(zoomy_ctx *c, const StageArgs<T> &a, int stage)
 template <typename T>
 static zoomy_status run_steps(zoomy_ctx *c, T *Q, int64_t ld, double dt, int nsteps)
 {
+    if constexpr (sizeof(T) == 4) {
+        if (c->closure_on) return closure_run_steps(c, Q, ld, dt, nsteps);
+    }
     T *Q1 = (T *)c->q1;
     if (dt <= 0.0) {
         cudaError_t e = launch_wavespeed<T>(c->dim, c->level, Q, ld, c->nc, T(c->g), T(c->hdry), c->ctl, 0, c->nsm,
@@ -588,5 +592,26 @@ extern "C" zoomy_status zoomy_autotune(zoomy_ctx *c, const void *Q, int64_t ld, 
     c->warps_per_block = W;
     if (rows_per_warp_out) *rows_per_warp_out = H;
     if (us_per_step_out) *us_per_step_out = us;
+    return ZOOMY_OK;
+}
+
+extern "C" zoomy_status zoomy_closure_set(zoomy_ctx *c, const float *params, const float *in_scale,
+                                          const float *out_scale, double lambda)
+{
+    if (!c || !params || !in_scale || !out_scale) return set_error(ZOOMY_EINVAL, "zoomy_closure_set: NULL argument");
+    if (!c->model_ok || c->kind != ZOOMY_MESH_2D || c->level != 1 || c->dtype != ZOOMY_FP32)
+        return set_error(ZOOMY_EINVAL, "zoomy_closure_set: needs a structured 2D level-1 FP32 model");
+    if (!(lambda >= 0.0)) return set_error(ZOOMY_EINVAL, "zoomy_closure_set: lambda >= 0");
+    zoomy_status st = closure_upload(c, params, in_scale, out_scale);
+    if (st != ZOOMY_OK) return st;
+    c->closure_on = true;
+    c->closure_lambda = lambda;
+    return ZOOMY_OK;
+}
+
+extern "C" zoomy_status zoomy_closure_clear(zoomy_ctx *c)
+{
+    if (!c) return set_error(ZOOMY_EINVAL, "zoomy_closure_clear: NULL context");
+    c->closure_on = false;
     return ZOOMY_OK;
 }

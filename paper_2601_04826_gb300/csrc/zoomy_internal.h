@@ -47,6 +47,10 @@ struct zoomy_ctx {
     std::vector<cudaEvent_t> prof_events;  // pool, reused
     std::vector<int> prof_kind;            // stage of each recorded (start, stop) pair
     size_t prof_used = 0;                  // events in use
+    // learned closure (fv_closure.cu): level-1 model closed with predicted level-4 moments
+    void *closure_d = nullptr;
+    bool closure_on = false;
+    double closure_lambda = 0.0;
     // ensemble (fv_ensemble.cu)
     void *ens = nullptr;
     // triangle mesh (device)
@@ -67,5 +71,8 @@ zoomy_status check_step_args(zoomy_ctx *c, const void *Q, int64_t ld, double dt,
 zoomy_status create_tri_mesh(const zoomy_mesh_desc *d, void *stream, zoomy_ctx **out);
 void tri_free(zoomy_ctx *c);
 void ens_free(zoomy_ctx *c);
+// learned closure (fv_closure.cu)
+zoomy_status closure_run_steps(zoomy_ctx *c, float *Q, int64_t ld, double dt, int nsteps);
+zoomy_status closure_upload(zoomy_ctx *c, const float *params, const float *in_scale, const float *out_scale);
 zoomy_status tri_run_steps(zoomy_ctx *c, float *Q, int64_t ld, double dt, int nsteps);
 }  // namespace zoomy

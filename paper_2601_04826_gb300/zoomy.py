@@ -63,6 +63,9 @@ _SIGNATURES = [
     ("zoomy_tune_set", C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
     ("zoomy_autotune", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_char_p, C.POINTER(C.c_int32),
                                  C.POINTER(C.c_double)]),
+    ("zoomy_closure_set", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double]),
+    ("zoomy_closure_clear", C.c_int, [C.c_void_p]),
+    ("zoomy_closure_eval", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]),
     ("zoomy_ensemble_create", C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_double,
                                         C.c_double, C.c_double, C.c_void_p, C.POINTER(C.c_void_p)]),
     ("zoomy_ensemble_offsets", C.c_int, [C.c_void_p, C.c_void_p]),
@@ -207,6 +210,23 @@ def zoomy_autotune(ctx, Q, ld, cache_path=None):
     _check(lib().zoomy_autotune(ctx, _ptr(Q), ld, cache_path.encode() if cache_path else None, C.byref(h),
                                 C.byref(us)))
     return h.value, us.value
+
+
+def zoomy_closure_set(ctx, params, in_scale, out_scale, lam):
+    import numpy as np
+
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    i = np.ascontiguousarray(in_scale, dtype=np.float32)
+    o = np.ascontiguousarray(out_scale, dtype=np.float32)
+    _check(lib().zoomy_closure_set(ctx, p.ctypes.data, i.ctypes.data, o.ctypes.data, lam))
+
+
+def zoomy_closure_clear(ctx):
+    _check(lib().zoomy_closure_clear(ctx))
+
+
+def zoomy_closure_eval(ctx, feat, out, n):
+    _check(lib().zoomy_closure_eval(ctx, _ptr(feat), _ptr(out), n))
 
 
 def zoomy_ensemble_create(sides, slip, level, nu=0.01, g=9.81, cfl=0.45, h_dry=1e-6, stream=None):

@@ -1,0 +1,123 @@
+"""The learned-closure solver on the GPU against the oracle's closure model.
+
+* zero network: the closure kernel reproduces the plain level-1 scheme (oracle and GPU);
+* bias-only network (constant predicted moments, exact in BF16): the fused kernel's restricted
+  level-4 face terms, Newtonian source and frozen-closure bottom stress match the oracle to 1e-5;
+* the tensor-core MLP alone (zoomy_closure_eval) matches the FP64 MLP with BF16 layer inputs within
+  a BF16 bound (relative L2 2e-2, cosine >= 0.999);
+* a full network: the closed solver matches the oracle within the bound the BF16 MLP allows.
+"""
+import numpy as np
+import pytest
+
+from gpu_util import rel_l1, rounded, to_device
+from oracle import mlp
+from paper_2601_04826_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+G = 9.81
+
+
+@pytest.fixture(scope="module")
+def Z():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_04826_gb300 import build, zoomy
+
+    build.build()
+    return zoomy
+
+
+def run_closure(Z, oracle, params, ins, outs, nx, ny, nsteps, Q0, bed, C=0.1, nu=0.01, bc=(1, 0, 1, 1)):
+    Q0r, bedr = rounded(Q0, 0), rounded(bed, 0)
+    ctx = Z.Context(Z.mesh_2d(nx, ny, bc=bc, bathymetry=bedr), 1, Z.friction(1, C=C, nu=nu), dtype=0)
+    Z.zoomy_closure_set(ctx.ctx, params, ins, outs, C)
+    Q = to_device(Q0r, 0)
+    tg = ctx.step(Q, nsteps=nsteps, dt=0.0)
+    got = Q.double().cpu().numpy()
+    ctx.close()
+    p32 = mlp.unpack(np.asarray(params, dtype=np.float32).astype(np.float64))
+    for k in ("W1", "W2", "W3"):  # the kernel holds BF16 weights
+        p32[k] = mlp.round_bf16(p32[k])
+    cl = oracle.Closure(mlp.pack(p32), np.float32(ins).astype(np.float64), np.float32(outs).astype(np.float64),
+                        bf16=True)
+    m4 = oracle.Model(4, 2, g=G, h_dry=1e-6, friction=1, C=C, nu=nu)
+    mesh = oracle.Mesh.rect(nx, ny, 0, 1, 0, 1, bc=bc)
+    ref, tr = oracle.step_closure(m4, cl, mesh, Q0r, nsteps, bed=bedr)
+    return got, ref, tg, tr
+
+
+def state(nx, ny, seed):
+    Q0 = inputs.random_moments_2d(nx, ny, 1, seed=seed, vel=0.25)
+    _, bed = inputs.gaussian_bump_2d(nx, ny, 1, seed=seed + 1)
+    return Q0, bed
+
+
+def test_zero_network_is_level1(Z, oracle):
+    nx, ny = 95, 67
+    Q0, bed = state(nx, ny, 1)
+    got, ref, tg, tr = run_closure(Z, oracle, np.zeros(mlp.NPARAMS), np.ones(6), np.ones(6), nx, ny, 20, Q0, bed)
+    assert np.all(rel_l1(got, ref) <= 1e-5), rel_l1(got, ref)
+    m1 = oracle.Model(1, 2, g=G, h_dry=1e-6, friction=1, C=0.1, nu=0.01)
+    ref1, _ = oracle.step(m1, oracle.Mesh.rect(nx, ny, 0, 1, 0, 1, bc=(1, 0, 1, 1)), rounded(Q0, 0), 20,
+                          bed=rounded(bed, 0))
+    assert np.all(rel_l1(got, ref1) <= 1e-5)
+
+
+def test_constant_closure_fv_parity(Z, oracle):
+    nx, ny = 88, 61
+    Q0, bed = state(nx, ny, 3)
+    p = {k: np.zeros_like(v) for k, v in mlp.init_params(0).items()}
+    p["b3"] = np.array([0.125, -0.0625, 0.03125, -0.09375, 0.046875, -0.015625])  # exact in BF16/FP32
+    got, ref, tg, tr = run_closure(Z, oracle, mlp.pack(p), np.ones(6), np.ones(6), nx, ny, 20, Q0, bed)
+    err = rel_l1(got, ref)
+    assert np.all(err <= 1e-5), err
+    assert tg == pytest.approx(tr, rel=1e-5)
+
+
+def test_mlp_eval_matches_oracle(Z, oracle):
+    import torch
+
+    rng = np.random.default_rng(2)
+    p = mlp.init_params(7)
+    for k in p:
+        p[k] = p[k] + 0.05 * rng.normal(size=p[k].shape)
+    ins = np.array([1.0, 2.0, 2.0, 4.0, 4.0, 5.0])
+    outs = np.array([0.1, 0.05, 0.02, 0.1, 0.05, 0.02])
+    nx = ny = 16
+    ctx = Z.Context(Z.mesh_2d(nx, ny), 1, Z.friction(1, C=0.1, nu=0.01), dtype=0)
+    Z.zoomy_closure_set(ctx.ctx, mlp.pack(p), ins, outs, 0.1)
+    n = 3001
+    F = np.stack([rng.uniform(0.5, 1.5, n), rng.uniform(-0.5, 0.5, n), rng.uniform(-0.5, 0.5, n),
+                  rng.uniform(-0.3, 0.3, n), rng.uniform(-0.3, 0.3, n), rng.uniform(0.05, 0.3, n)])
+    Fd = torch.tensor(F, dtype=torch.float32, device="cuda")
+    Od = torch.zeros_like(Fd)
+    Z.zoomy_closure_eval(ctx.ctx, Fd, Od, n)
+    torch.cuda.synchronize()
+    got = Od.double().cpu().numpy().T
+    ctx.close()
+    p32 = mlp.unpack(np.asarray(mlp.pack(p), dtype=np.float32).astype(np.float64))
+    for k in ("W1", "W2", "W3"):
+        p32[k] = mlp.round_bf16(p32[k])
+    ref, _ = mlp.forward(p32, np.float32(F.T).astype(np.float64) * np.float32(ins), bf16_inputs=True)
+    ref = ref * np.float32(outs)
+    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    cos = np.sum(got * ref) / (np.linalg.norm(got) * np.linalg.norm(ref))
+    assert rel < 2e-2 and cos > 0.999, (rel, cos)
+
+
+def test_random_network_closed_solver(Z, oracle):
+    nx, ny = 70, 52
+    Q0, bed = state(nx, ny, 5)
+    rng = np.random.default_rng(11)
+    p = mlp.init_params(9)
+    for k in p:
+        p[k] = 0.5 * p[k] + 0.02 * rng.normal(size=p[k].shape)
+    ins = np.array([1.0, 2.0, 2.0, 4.0, 4.0, 5.0])
+    outs = np.full(6, 0.05)
+    got, ref, tg, tr = run_closure(Z, oracle, mlp.pack(p), ins, outs, nx, ny, 10, Q0, bed)
+    err = rel_l1(got, ref)
+    print("closed solver relative L1", err)
+    assert np.all(err <= 1e-4), err
