@@ -177,6 +177,39 @@ zoomy_status zoomy_closure_clear(zoomy_ctx *ctx);
  * features) -> out (device, SoA [6][n], the six predicted moments).  Queued on the context's stream. */
 zoomy_status zoomy_closure_eval(zoomy_ctx *ctx, const float *feat, float *out, int64_t n);
 
+/* ---- Training the closure MLP ------------------------------------------------------------------
+ * Full-batch (or caller-sliced mini-batch) training of the closure network above by hand-written
+ * kernels: forward and backward passes one thread per sample (FP32, weights in shared memory), the
+ * weight gradients as split-K reductions summed in a fixed order (deterministic), Adam (Kingma &
+ * Ba: beta1 0.9, beta2 0.999, eps 1e-8) on FP32 master weights.  Loss = mean over the n samples and
+ * the 6 outputs of (y - t)^2 in the scaled output space.  X: device [n][6] scaled features, T:
+ * device [n][6] scaled targets (row-major, sample-major).  The paper builds no learned closure; this
+ * trains the "material closure" of Sec. 1 / Sec. 3.4 as a data-driven one.
+ *   zoomy_mlp_create: params = 4998 host floats in the order of zoomy_closure_set; stream = the
+ *     stream every later call queues on (NULL = legacy default stream).
+ *   zoomy_mlp_grad: loss (host, may be NULL) and gradient (host [4998], may be NULL) of the current
+ *     parameters; synchronises the stream when either is requested.
+ *   zoomy_mlp_train_step: one Adam step with learning rate lr > 0 on the batch; loss (may be NULL:
+ *     no synchronisation) is the loss BEFORE the step.
+ *   zoomy_mlp_get_params: the current FP32 parameters into host params [4998] (synchronises).
+ * The workspace grows to the largest n seen (~1.6 kB per sample).  ZOOMY_EINVAL on NULL pointers,
+ * n < 1 or lr <= 0; ZOOMY_ECUDA on launch or allocation failures. */
+typedef struct zoomy_mlp zoomy_mlp; /* opaque, library-owned */
+zoomy_status zoomy_mlp_create(const float *params, void *stream, zoomy_mlp **out);
+zoomy_status zoomy_mlp_destroy(zoomy_mlp *mlp);
+zoomy_status zoomy_mlp_get_params(zoomy_mlp *mlp, float *params);
+zoomy_status zoomy_mlp_grad(zoomy_mlp *mlp, const float *X, const float *T, int64_t n, float *loss, float *grad);
+zoomy_status zoomy_mlp_train_step(zoomy_mlp *mlp, const float *X, const float *T, int64_t n, float lr, float *loss);
+
+/* Training samples from a structured 2D level-`level` FP32 state Q[v][ld] (device): for each of the
+ * n listed cells (device int64 indices), X[s] = (h, u_m, v_m, alpha_1, beta_1, lambda) * in_scale and
+ * T[s] = (alpha_2, alpha_3, alpha_4, beta_2, beta_3, beta_4) / out_scale (moments above `level` are
+ * zero; velocities are zero where h <= h_dry).  in_scale / out_scale: device [6]; X, T: device
+ * [n][6].  Queued on `stream`. */
+zoomy_status zoomy_closure_samples(const float *Q, int64_t ld, int32_t level, const int64_t *cells, int64_t n,
+                                   double lambda, double h_dry, const float *in_scale, const float *out_scale,
+                                   float *X, float *T, void *stream);
+
 /* ---- Batched ensembles (independent runs of uneven sizes in one launch) -------------------------
  * nmembers square grids of side sides[m] on the unit square with walls, each with its own slip
  * coefficient C[m] (Navier slip, rho = 1) and the Newtonian viscosity nu, level `level`, FP32

@@ -66,6 +66,15 @@ _SIGNATURES = [
     ("zoomy_closure_set", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double]),
     ("zoomy_closure_clear", C.c_int, [C.c_void_p]),
     ("zoomy_closure_eval", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]),
+    ("zoomy_mlp_create", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
+    ("zoomy_mlp_destroy", C.c_int, [C.c_void_p]),
+    ("zoomy_mlp_get_params", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("zoomy_mlp_grad", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_float),
+                                 C.c_void_p]),
+    ("zoomy_mlp_train_step", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float,
+                                       C.POINTER(C.c_float)]),
+    ("zoomy_closure_samples", C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_double,
+                                        C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("zoomy_ensemble_create", C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_double,
                                         C.c_double, C.c_double, C.c_void_p, C.POINTER(C.c_void_p)]),
     ("zoomy_ensemble_offsets", C.c_int, [C.c_void_p, C.c_void_p]),
@@ -227,6 +236,47 @@ def zoomy_closure_clear(ctx):
 
 def zoomy_closure_eval(ctx, feat, out, n):
     _check(lib().zoomy_closure_eval(ctx, _ptr(feat), _ptr(out), n))
+
+
+def zoomy_mlp_create(params, stream=None):
+    import numpy as np
+
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    h = C.c_void_p()
+    _check(lib().zoomy_mlp_create(p.ctypes.data, _stream(stream), C.byref(h)))
+    return h.value
+
+
+def zoomy_mlp_destroy(mlp):
+    _check(lib().zoomy_mlp_destroy(mlp))
+
+
+def zoomy_mlp_get_params(mlp):
+    import numpy as np
+
+    p = np.zeros(4998, dtype=np.float32)
+    _check(lib().zoomy_mlp_get_params(mlp, p.ctypes.data))
+    return p
+
+
+def zoomy_mlp_grad(mlp, X, T, n):
+    import numpy as np
+
+    loss = C.c_float()
+    g = np.zeros(4998, dtype=np.float32)
+    _check(lib().zoomy_mlp_grad(mlp, _ptr(X), _ptr(T), n, C.byref(loss), g.ctypes.data))
+    return loss.value, g
+
+
+def zoomy_mlp_train_step(mlp, X, T, n, lr, want_loss=False):
+    loss = C.c_float()
+    _check(lib().zoomy_mlp_train_step(mlp, _ptr(X), _ptr(T), n, lr, C.byref(loss) if want_loss else None))
+    return loss.value if want_loss else None
+
+
+def zoomy_closure_samples(Q, ld, level, cells, n, lam, h_dry, in_scale, out_scale, X, T, stream=None):
+    _check(lib().zoomy_closure_samples(_ptr(Q), ld, level, _ptr(cells), n, lam, h_dry, _ptr(in_scale),
+                                       _ptr(out_scale), _ptr(X), _ptr(T), _stream(stream)))
 
 
 def zoomy_ensemble_create(sides, slip, level, nu=0.01, g=9.81, cfl=0.45, h_dry=1e-6, stream=None):
