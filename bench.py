@@ -73,6 +73,18 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def peaks_tensor():
+    """Dense BF16 tensor peak in TFLOP/s: the measured sustained cuBLAS figure (a kernel timed inside a
+    long run), else the fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        v = d.get("bf16_tflops_sustained") or d.get("bf16_tflops")
+        if v:
+            return float(v), "measured sustained" if d.get("bf16_tflops_sustained") else "measured burst"
+    return 1700.0, "fallback"
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -333,6 +345,86 @@ def run_ensemble(args):
             "gpu_launches": 1, "clocks": clk.summary()}
 
 
+def run_closure(args):
+    """Config-5 workload: train the closure on seeded level-4 runs, then time-to-solution at T = 2 on a
+    1024^2 held-out member: plain level 4 against level 1 closed by the network (and plain level 1),
+    with the relative L1 errors of (h, h u_m, h v_m) against level 4.  Prints its own JSON line."""
+    import time
+
+    import numpy as np
+    import torch
+
+    from paper_2601_04826_gb300 import build, closure, inputs, zoomy
+
+    build.build()
+    T, side = 2.0, 1024
+    t0 = time.perf_counter()
+    F, Y, _ = closure.generate_samples(nmembers=args.closure_members, side=args.closure_train_side, level=4, T=T,
+                                       snapshots=8, seed=3)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    ins, outs = closure.scales(F, Y)
+    t0 = time.perf_counter()
+    params, hist = closure.fit(F, Y, ins, outs, steps=3000, batch=16384, seed=0)
+    t_train = time.perf_counter() - t0
+    nsamples = int(F.shape[0])
+    del F, Y
+    torch.cuda.empty_cache()
+    _, lam, seeds = inputs.ensemble_members(1, seed=4242)
+    lam, seed = float(lam[0]), int(seeds[0])
+    res = {}
+    with ClockSampler(0) as clk:
+        for name, lv, cl in (("level4", 4, None), ("closure", 1, (params, ins, outs)), ("level1", 1, None)):
+            r = closure.Run(side, lv, lam, seed, closure=cl)
+            if cl is None:
+                r.ctx.autotune(r.Q)
+            r.ctx.step(r.Q, nsteps=3, dt=1e-6)  # warm-up (module load, first launches)
+            r.Q.copy_(closure.Run.initial(side, lv, seed))
+            zoomy.zoomy_profile_enable(r.ctx.ctx, True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            nsteps = r.run_to(T)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            launches, kms = zoomy.zoomy_profile_read(r.ctx.ctx)
+            res[name] = {"time_s": wall, "steps": nsteps, "state": r.mean_state(),
+                         "kernel_ms": [kms[i] / max(launches[i], 1) for i in range(3)],
+                         "launches": int(sum(launches))}
+            r.close()
+    ref = res["level4"]["state"]
+
+    def l1(st):
+        return [float(v) for v in np.abs(st - ref).sum(axis=1) / np.abs(ref).sum(axis=1)]
+
+    cl_, l4 = res["closure"], res["level4"]
+    # tensor work of one prediction launch: one network evaluation per cell
+    flop_eval = 2 * (6 * 64 + 64 * 64 + 64 * 6)
+    cells = side * side
+    ach = flop_eval * cells / (cl_["kernel_ms"][2] * 1e-3) / 1e12
+    pk = peaks_tensor()
+    return {"metric": "time_to_solution", "value": cl_["time_s"], "unit": "s", "n_gpus": 1, "steps": cl_["steps"],
+            "warmup": 3, "ms_per_step": 1e3 * cl_["time_s"] / cl_["steps"], "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic (seeded Gaussian bumps)",
+            "config": {"workload": f"learned closure: level 1 + MLP on {side}x{side}, walls, T={T}, slip "
+                                   f"{lam:.4f} (held-out member), vs plain level 4",
+                       "training": {"members": args.closure_members, "side": args.closure_train_side,
+                                    "samples": nsamples, "adam_steps": 3000, "batch": 16384,
+                                    "data_s": t_data, "train_s": t_train, "loss": hist[-1][1]}},
+            "level4": {"time_s": l4["time_s"], "steps": l4["steps"], "ms_per_step": 1e3 * l4["time_s"] / l4["steps"]},
+            "level1": {"time_s": res["level1"]["time_s"], "steps": res["level1"]["steps"]},
+            "speedup_vs_level4": l4["time_s"] / cl_["time_s"],
+            "rel_l1_vs_level4": {"closure": l1(cl_["state"]), "level1": l1(res["level1"]["state"]),
+                                 "vars": ["h", "h u_m", "h v_m"]},
+            "roofline": {"bound": "tensor", "kernel": "k_closure_predict", "achieved": ach, "peak": pk[0],
+                         "peak_kind": pk[1], "unit": "TFLOP/s", "frac": ach / pk[0], "traffic": None,
+                         "algorithmic_flop_per_launch": flop_eval * cells,
+                         "avg_launch_ms": {"predict": cl_["kernel_ms"][2], "stage1": cl_["kernel_ms"][0],
+                                           "stage2": cl_["kernel_ms"][1]},
+                         "note": "network FLOPs (unpadded 6-64-64-6) of one prediction launch over its average "
+                                 "duration; BF16 operands, FP32 accumulation"},
+            "gpu_launches": int(cl_["launches"]), "clocks": clk.summary()}
+
+
 def oracle_window_run(side, nsteps):
     """The oracle on a side x side window of the workload (cells of the 2048^2 grid, walls)."""
     import numpy as np
@@ -409,9 +501,12 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
-    ap.add_argument("--workload", choices=["grid", "tri", "ensemble"], default="grid",
+    ap.add_argument("--workload", choices=["grid", "tri", "ensemble", "closure"], default="grid",
                     help="grid: the 2048^2 level-2 benchmark (default); tri: the ~4M-triangle level-3 dam break; "
-                         "ensemble: 512 ragged level-1 members in one persistent launch")
+                         "ensemble: 512 ragged level-1 members in one persistent launch; closure: learned "
+                         "closure vs level 4, time to T = 2 on 1024^2")
+    ap.add_argument("--closure-members", type=int, default=256, help="level-4 training runs (closure workload)")
+    ap.add_argument("--closure-train-side", type=int, default=128, help="grid side of the training runs")
     ap.add_argument("--rows-per-warp", type=int, default=0,
                     help="fixed structured-kernel segment height instead of the autotuner (profiling runs)")
     args = ap.parse_args()
@@ -431,6 +526,8 @@ def main():
         line = run_tri(args) if rank == 0 else None
     elif args.workload == "ensemble":
         line = run_ensemble(args) if rank == 0 else None
+    elif args.workload == "closure":
+        line = run_closure(args) if rank == 0 else None
     else:
         line = run_ours(args, rank, world, local_rank)
     if rank == 0 and line is not None:

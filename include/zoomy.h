@@ -145,7 +145,9 @@ zoomy_status zoomy_mass(zoomy_ctx *ctx, const void *Q, int64_t ld, double *out);
 
 /* Work decomposition of the structured 2D kernels (a performance knob; results do not depend
  * on it): each warp marches over rows_per_warp rows of a 30-column strip, warps_per_block warps
- * per CTA.  rows_per_warp in [1, 4096], warps_per_block in [1, 32]. */
+ * per CTA.  rows_per_warp in [1, 4096], warps_per_block in [1, 32].  Until this or zoomy_autotune
+ * sets it, rows_per_warp follows the grid: about 24 warps per SM (16 for the learned-closure stage),
+ * within [8, 64] rows. */
 zoomy_status zoomy_tune_set(zoomy_ctx *ctx, int32_t rows_per_warp, int32_t warps_per_block);
 
 /* Autotuner of the structured 2D decomposition: times both stage kernels on the state Q (device,
@@ -245,8 +247,8 @@ zoomy_status zoomy_ensemble_set_barrier(zoomy_ctx *ctx, int64_t spin_limit, int3
 /* Per-launch timing of the stage kernels with CUDA events recorded on the context's stream
  * around every stage launch (on = 1) or off (on = 0, default).  zoomy_profile_read waits for
  * the stream and returns the launch counts and the summed device time in milliseconds of the
- * stage-1 and stage-2 kernels since profiling was enabled, then resets the counters.  Arrays
- * of length 2 (host). */
+ * stage-1 kernels, the stage-2 kernels and the learned closure's prediction kernels (in that
+ * order) since profiling was enabled, then resets the counters.  Arrays of length 3 (host). */
 zoomy_status zoomy_profile_enable(zoomy_ctx *ctx, int32_t on);
 zoomy_status zoomy_profile_read(zoomy_ctx *ctx, int64_t *launches, double *total_ms);
 

@@ -134,8 +134,6 @@ class Run:
     network (closure=(params, in_scale, out_scale))."""
 
     def __init__(self, side, level, lam, member_seed, nu=0.01, cfl=0.45, h_dry=1e-6, closure=None):
-        import torch
-
         lv = 1 if closure is not None else level
         self.ctx = zoomy.Context(zoomy.mesh_2d(side, side, bc=(1, 1, 1, 1)), lv,
                                  zoomy.friction(zoomy.FRICTION_SLIP_NEWTONIAN, C=lam, nu=nu), g=G, cfl=cfl,
@@ -144,8 +142,19 @@ class Run:
         if closure is not None:
             p, i, o = closure
             zoomy.zoomy_closure_set(self.ctx.ctx, p, i, o, lam)
-        Q0, _ = inputs.gaussian_bump_2d(side, side, lv, seed=int(member_seed), bathymetry=False)
-        self.Q = torch.tensor(Q0, dtype=torch.float32, device="cuda")
+        self.Q = self.initial(side, lv, member_seed)
+
+    @staticmethod
+    def initial(side, level, member_seed):
+        """The member's initial state (the ensemble workload's Gaussian bump at rest, flat bed)."""
+        import torch
+
+        Q0, _ = inputs.gaussian_bump_2d(side, side, level, seed=int(member_seed), bathymetry=False)
+        return torch.tensor(Q0, dtype=torch.float32, device="cuda")
+
+    def autotune(self):
+        """Tune the structured decomposition of a plain level-N run (the closed stage sizes its own)."""
+        return self.ctx.autotune(self.Q)
 
     def run_to(self, T):
         return advance_to(self.ctx, self.Q, T)

@@ -41,6 +41,8 @@ struct ClosureDev {
 struct ClosureArgs {
     StageArgs<float> s;
     const ClosureDev *net;
+    float *pred;      // predicted closed moments of the stage input, SoA [6][pstride]
+    int64_t pstride;  // nx * ny
     float lambda;
 };
 
@@ -337,16 +339,6 @@ __global__ void __launch_bounds__(128) k_stage_closure(ClosureArgs ca)
 {
     const StageArgs<float> &a = ca.s;
     constexpr unsigned F = 0xffffffffu;
-    __shared__ ClosureDev net;
-    __shared__ uint32_t xs_all[4][32 * 4];
-    __shared__ float ys_all[4][32 * 8];
-    // the network's fragments into shared memory (one copy per CTA)
-    {
-        const uint32_t *src = reinterpret_cast<const uint32_t *>(ca.net);
-        uint32_t *dst = reinterpret_cast<uint32_t *>(&net);
-        for (int i = threadIdx.x; i < (int)(sizeof(ClosureDev) / 4); i += blockDim.x) dst[i] = src[i];
-    }
-    __syncthreads();
     if (*(volatile unsigned int *)&a.ctl->status) return;
     float dt;
     if (!step_dt(a, dt)) {
@@ -355,8 +347,6 @@ __global__ void __launch_bounds__(128) k_stage_closure(ClosureArgs ca)
     }
     if (STAGE == 1 && blockIdx.x == 0 && threadIdx.x == 0) step_bookkeeping(a, dt);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t *xs = xs_all[warp];
-    float *ys = ys_all[warp];
     const int wg = blockIdx.x * 4 + warp;
     const int strip = wg % a.nstrips, seg = wg / a.nstrips;
     if (seg >= a.nsegs) return;
@@ -374,7 +364,6 @@ __global__ void __launch_bounds__(128) k_stage_closure(ClosureArgs ca)
         make_crec(prev, 0.0f, 0.0f, q0, z, false, false, hdry);
     }
     float xprev[CL_NV] = {0, 0, 0, 0, 0}, accp[CL_NV] = {0, 0, 0, 0, 0};
-    float smax = 0.0f;
     unsigned flag = 0;
     for (int r = r0 - 1; r <= r1; ++r) {
         const int rs = r < 0 ? 0 : (r >= a.ny ? a.ny - 1 : r);
@@ -384,10 +373,10 @@ __global__ void __launch_bounds__(128) k_stage_closure(ClosureArgs ca)
 #pragma unroll
         for (int v = 0; v < CL_NV; ++v) x[v] = __ldg(a.X + v * a.ld + idx);
         const float bed = __ldg(a.bed + idx);
-        // closure of this row's cells (features of the unreflected state; ghosts reflect the result)
-        float f[6], pred[6];
-        features(x, ca.lambda, hdry, f);
-        mlp_warp(&net, f, pred, xs, ys, lane);
+        // closure of this row's cells (predicted from the unreflected state; ghosts reflect it)
+        float pred[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) pred[j] = __ldg(ca.pred + j * ca.pstride + idx);
         float q[CL_NV];
 #pragma unroll
         for (int v = 0; v < CL_NV; ++v) q[v] = x[v];
@@ -469,17 +458,13 @@ __global__ void __launch_bounds__(128) k_stage_closure(ClosureArgs ca)
                 if (STAGE == 2) {
 #pragma unroll
                     for (int v = 0; v < CL_NV; ++v) y[v] = 0.5f * (a.Qn[v * a.ld + oidx] + y[v]);
-                    // wave speed of the new state's closed profile (for the next step's dt)
-                    float fo[6], po[6];
-                    features(y, ca.lambda, hdry, fo);
-                    mlp_warp(&net, fo, po, xs, ys, lane);
-                    CRec ro;
-                    make_crec(ro, y[0], 0.0f, y, po, false, false, hdry);
-                    const float sp = ro.um + sqrtf(g * fmaxf(y[0], 0.0f) + ro.s2) + ro.s1;
+                    // (the next step's prediction kernel takes the new state's wave speed)
                     if (owned) {
-                        if (!(sp <= 3.0e38f)) flag |= DEV_NAN;
-                        if (!(y[0] >= 0.0f)) flag |= (y[0] < 0.0f) ? DEV_NEGDEPTH : DEV_NAN;
-                        smax = (sp > smax || sp != sp) ? sp : smax;
+                        bool bad = false;
+#pragma unroll
+                        for (int v = 0; v < CL_NV; ++v) bad |= !(fabsf(y[v]) <= 3.0e38f);
+                        if (bad) flag |= DEV_NAN;
+                        if (y[0] < 0.0f) flag |= DEV_NEGDEPTH;
                     }
                 }
                 if (owned) {
@@ -495,14 +480,15 @@ __global__ void __launch_bounds__(128) k_stage_closure(ClosureArgs ca)
             accp[v] = accc[v];
         }
     }
-    if (STAGE == 2) {
-        if (flag) atomicOr(&a.ctl->status, flag);
-        reduce_smax<float>(a.ctl, a.slot_out, smax);
-    }
+    if (STAGE == 2 && flag) atomicOr(&a.ctl->status, flag);
 }
 
-// Initial wave speeds of the closed state (first dt of a call).
-__global__ void __launch_bounds__(128) k_closure_wavespeed(ClosureArgs ca)
+// The closure of every cell of the stage input X: predicted moments into ca.pred, and (WS) the
+// maximum wave speed of the closed profiles into the control slot a.slot_out, plus the
+// non-finite / negative-depth flags of X.  The stage kernels then read the predictions of their
+// cells and of the halo cells.
+template <bool WS>
+__global__ void __launch_bounds__(128) k_closure_predict(ClosureArgs ca)
 {
     const StageArgs<float> &a = ca.s;
     __shared__ ClosureDev net;
@@ -514,6 +500,7 @@ __global__ void __launch_bounds__(128) k_closure_wavespeed(ClosureArgs ca)
         for (int i = threadIdx.x; i < (int)(sizeof(ClosureDev) / 4); i += blockDim.x) dst[i] = src[i];
     }
     __syncthreads();
+    if (*(volatile unsigned int *)&a.ctl->status) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t nc = (int64_t)a.nx * a.ny;
     float smax = 0.0f;
@@ -524,21 +511,29 @@ __global__ void __launch_bounds__(128) k_closure_wavespeed(ClosureArgs ca)
         const int64_t ic = i < nc ? i : nc - 1;
         float x[CL_NV];
 #pragma unroll
-        for (int v = 0; v < CL_NV; ++v) x[v] = a.X[v * a.ld + ic];
+        for (int v = 0; v < CL_NV; ++v) x[v] = __ldg(a.X + v * a.ld + ic);
         float f[6], p[6];
         features(x, ca.lambda, a.hdry, f);
         mlp_warp(&net, f, p, xs_all[warp], ys_all[warp], lane);
-        CRec r;
-        make_crec(r, x[0], 0.0f, x, p, false, false, a.hdry);
-        const float s = r.um + sqrtf(a.g * fmaxf(x[0], 0.0f) + r.s2) + r.s1;
         if (i < nc) {
-            if (!(s <= 3.0e38f)) flag |= DEV_NAN;
-            if (!(x[0] >= 0.0f)) flag |= (x[0] < 0.0f) ? DEV_NEGDEPTH : DEV_NAN;
-            smax = (s > smax || s != s) ? s : smax;
+#pragma unroll
+            for (int j = 0; j < 6; ++j) ca.pred[j * ca.pstride + i] = p[j];
+        }
+        if (WS) {
+            CRec r;
+            make_crec(r, x[0], 0.0f, x, p, false, false, a.hdry);
+            const float s = r.um + sqrtf(a.g * fmaxf(x[0], 0.0f) + r.s2) + r.s1;
+            if (i < nc) {
+                if (!(s <= 3.0e38f)) flag |= DEV_NAN;
+                if (!(x[0] >= 0.0f)) flag |= (x[0] < 0.0f) ? DEV_NEGDEPTH : DEV_NAN;
+                smax = (s > smax || s != s) ? s : smax;
+            }
         }
     }
-    if (flag) atomicOr(&a.ctl->status, flag);
-    reduce_smax<float>(a.ctl, 0, smax);
+    if (WS) {
+        if (flag) atomicOr(&a.ctl->status, flag);
+        reduce_smax<float>(a.ctl, a.slot_out, smax);
+    }
 }
 
 // The closure MLP alone on n feature vectors (SoA [6][n] -> [6][n]), same device code as in the stage.
@@ -633,33 +628,41 @@ zoomy_status closure_run_steps(zoomy_ctx *c, float *Q, int64_t ld, double dt, in
     a.dmin = c->min_delta;
     a.dt_fixed = dt;
     a.ctl = c->ctl;
-    a.H = c->rows_per_warp;
     a.nstrips = (int)((c->nx + 29) / 30);
+    a.H = c->rows_per_warp > 0 ? c->rows_per_warp : rows_per_warp_for(c->nx, c->ny, c->nsm, 16);
     a.nsegs = (int)((c->ny + a.H - 1) / a.H);
     ca.net = (const ClosureDev *)c->closure_d;
+    ca.pred = (float *)c->closure_pred;
+    ca.pstride = c->nx * c->ny;
     ca.lambda = (float)c->closure_lambda;
     float *Q1 = (float *)c->q1;
     const int nwarps = a.nstrips * a.nsegs;
     dim3 grid((nwarps + 3) / 4), block(128);
-    if (dt <= 0.0) {
-        a.X = Q;
-        k_closure_wavespeed<<<4 * c->nsm, 128, 0, c->stream>>>(ca);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_fail(e, "closure wavespeed launch");
-    }
+    const unsigned pgrid = (unsigned)(4 * c->nsm);
     for (int k = 0; k < nsteps; ++k) {
+        // closure of Q^n and its wave speed (this step's dt) into slot k & 1, cleared by the previous
+        // step's first stage (or at the start of the call)
+        a.X = Q;
+        a.slot_out = k & 1;
+        zoomy_status ps = prof_mark(c, 3, true);
+        if (ps != ZOOMY_OK) return ps;
+        k_closure_predict<true><<<pgrid, 128, 0, c->stream>>>(ca);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "closure prediction launch");
+        if ((ps = prof_mark(c, 3, false)) != ZOOMY_OK) return ps;
         a.slot_in = k & 1;
         a.slot_out = (k + 1) & 1;
-        a.X = Q;
         a.Qn = Q;
         a.out = Q1;
-        zoomy_status ps = prof_mark(c, 1, true);
-        if (ps != ZOOMY_OK) return ps;
+        if ((ps = prof_mark(c, 1, true)) != ZOOMY_OK) return ps;
         k_stage_closure<1><<<grid, block, 0, c->stream>>>(ca);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_fail(e, "closure stage 1 launch");
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "closure stage 1 launch");
         if ((ps = prof_mark(c, 1, false)) != ZOOMY_OK) return ps;
         a.X = Q1;
+        if ((ps = prof_mark(c, 3, true)) != ZOOMY_OK) return ps;
+        k_closure_predict<false><<<pgrid, 128, 0, c->stream>>>(ca);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "closure prediction launch");
+        if ((ps = prof_mark(c, 3, false)) != ZOOMY_OK) return ps;
         a.Qn = Q;
         a.out = Q;
         if ((ps = prof_mark(c, 2, true)) != ZOOMY_OK) return ps;
@@ -676,6 +679,10 @@ zoomy_status closure_upload(zoomy_ctx *c, const float *params, const float *in_s
     build_closure_dev(params, in_scale, out_scale, d);
     if (!c->closure_d) {
         cudaError_t e = cudaMalloc(&c->closure_d, sizeof(ClosureDev));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    }
+    if (!c->closure_pred) {
+        cudaError_t e = cudaMalloc(&c->closure_pred, sizeof(float) * 6 * (size_t)(c->nx * c->ny));
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
     }
     cudaError_t e = cudaMemcpy(c->closure_d, &d, sizeof(ClosureDev), cudaMemcpyHostToDevice);

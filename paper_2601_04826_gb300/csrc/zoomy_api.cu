@@ -115,6 +115,7 @@ extern "C" zoomy_status zoomy_mesh_destroy(zoomy_ctx *c)
     cudaFree(c->q1);
     cudaFree(c->qdev_host);
     cudaFree(c->closure_d);
+    cudaFree(c->closure_pred);
     for (cudaEvent_t ev : c->prof_events) cudaEventDestroy(ev);
     tri_free(c);
     ens_free(c);
@@ -235,7 +236,7 @@ static void fill_args(zoomy_ctx *c, StageArgs<T> &a, int64_t ld, double dt)
     a.dmin = c->min_delta;
     a.dt_fixed = dt;
     a.ctl = c->ctl;
-    a.H = c->rows_per_warp;
+    a.H = c->rows_per_warp > 0 ? c->rows_per_warp : rows_per_warp_for(c->nx, c->ny, c->nsm, 24);
     a.nstrips = (int)((c->nx + 29) / 30);
     a.nsegs = (int)((c->ny + a.H - 1) / a.H);
 }
@@ -440,8 +441,8 @@ extern "C" zoomy_status zoomy_profile_read(zoomy_ctx *c, int64_t *launches, doub
 {
     if (!c || !launches || !total_ms) return set_error(ZOOMY_EINVAL, "zoomy_profile_read: NULL argument");
     ZCHECK(cudaStreamSynchronize(c->stream));
-    launches[0] = launches[1] = 0;
-    total_ms[0] = total_ms[1] = 0.0;
+    launches[0] = launches[1] = launches[2] = 0;
+    total_ms[0] = total_ms[1] = total_ms[2] = 0.0;
     for (size_t k = 0; k < c->prof_kind.size(); ++k) {
         float ms = 0.f;
         ZCHECK(cudaEventElapsedTime(&ms, c->prof_events[2 * k], c->prof_events[2 * k + 1]));

@@ -41,7 +41,7 @@ struct zoomy_ctx {
     zoomy::DevCtl *ctl_aux = nullptr;  // scratch of the synchronous reductions
     double *partials = nullptr;
     // structured 2D decomposition (rows per warp segment, warps per block)
-    int rows_per_warp = 64, warps_per_block = 4;
+    int rows_per_warp = 0, warps_per_block = 4;  // rows_per_warp 0: rows_per_warp_for()
     // stage-kernel profiling (zoomy_profile_enable)
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_events;  // pool, reused
@@ -49,6 +49,7 @@ struct zoomy_ctx {
     size_t prof_used = 0;                  // events in use
     // learned closure (fv_closure.cu): level-1 model closed with predicted level-4 moments
     void *closure_d = nullptr;
+    void *closure_pred = nullptr;  // predicted closed moments of the current stage input [6][nx ny]
     bool closure_on = false;
     double closure_lambda = 0.0;
     // ensemble (fv_ensemble.cu)
@@ -60,6 +61,15 @@ struct zoomy_ctx {
 };
 
 namespace zoomy {
+// Segment height of the structured 2D row-marching kernels when none was set: about
+// warps_per_sm warps per SM over the grid (30-column strips), within [8, 64] rows.
+inline int rows_per_warp_for(int64_t nx, int64_t ny, int nsm, int warps_per_sm)
+{
+    const int64_t want = (int64_t)(nsm > 0 ? nsm : 1) * warps_per_sm;
+    const int64_t H = ((nx + 29) / 30) * ny / want;
+    return (int)(H < 8 ? 8 : (H > 64 ? 64 : H));
+}
+
 zoomy_status set_error(zoomy_status st, const char *fmt, ...);
 zoomy_status cuda_fail(cudaError_t e, const char *where);
 zoomy_status ctx_init_device(zoomy_ctx *c);

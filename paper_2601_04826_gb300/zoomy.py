@@ -322,8 +322,8 @@ def zoomy_profile_enable(ctx, on=True):
 
 
 def zoomy_profile_read(ctx):
-    n = (C.c_int64 * 2)()
-    ms = (C.c_double * 2)()
+    n = (C.c_int64 * 3)()
+    ms = (C.c_double * 3)()
     _check(lib().zoomy_profile_read(ctx, n, ms))
     return list(n), list(ms)
 
