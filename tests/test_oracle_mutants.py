@@ -31,9 +31,13 @@ MUTANTS = {
     "rk2_average_dropped": ("for (int64_t k = 0; k < n; ++k) Q[k] = 0.5 * (Q[k] + Q2[k]);",
                            "for (int64_t k = 0; k < n; ++k) Q[k] = Q2[k];"),
     "hr_depth_not_clipped": ("if (hs < 0.0) hs = 0.0;", "(void)0;"),
+    "tri_normal_y_flipped": ("me->fny[t * 3 + f] = -ex / len;", "me->fny[t * 3 + f] = ex / len;"),
+    "tri_edge_length_unit": ("me->flen[t * 3 + f] = len;", "me->flen[t * 3 + f] = 1.0;"),
+    "tri_area_doubled": ("me->area[t] = sa;", "me->area[t] = 2.0 * sa;"),
 }
 
-PIN_TESTS = ["tests/test_oracle_basis.py", "tests/test_oracle_model.py", "tests/test_oracle_scheme.py"]
+PIN_TESTS = ["tests/test_oracle_basis.py", "tests/test_oracle_model.py", "tests/test_oracle_scheme.py",
+             "tests/test_oracle_triangles.py"]
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
