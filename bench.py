@@ -345,6 +345,46 @@ def run_ensemble(args):
             "gpu_launches": 1, "clocks": clk.summary()}
 
 
+def run_closure_kernels(args):
+    """The closed level-1 step alone on the 1024^2 closure workload with an untrained (Glorot) network:
+    per-kernel launch times of the prediction and stage kernels, for profiling runs.  Prints its own
+    JSON line (no training, no level-4 comparison)."""
+    import numpy as np
+    import torch
+
+    from paper_2601_04826_gb300 import build, closure, inputs, zoomy
+
+    build.build()
+    side = 1024
+    _, lam, seeds = inputs.ensemble_members(1, seed=4242)
+    params = closure.init_params(0)
+    ins = np.array([1.0, 4.0, 4.0, 50.0, 50.0, 4.0])
+    outs = np.full(6, 1e-3)
+    r = closure.Run(side, 1, float(lam[0]), int(seeds[0]), closure=(params, ins, outs))
+    zoomy.zoomy_closure_engine(r.ctx.ctx, args.closure_engine)
+    r.ctx.step(r.Q, nsteps=args.warmup, dt=0.0)
+    zoomy.zoomy_profile_enable(r.ctx.ctx, True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    r.ctx.step(r.Q, nsteps=args.steps, dt=0.0, sync=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    zoomy.zoomy_sync(r.ctx.ctx)
+    launches, kms = zoomy.zoomy_profile_read(r.ctx.ctx)
+    ms = e0.elapsed_time(e1)
+    r.close()
+    flop_eval = 2 * (6 * 64 + 64 * 64 + 64 * 6)
+    avg = [kms[i] / max(launches[i], 1) for i in range(3)]
+    return {"metric": "closed level-1 step time", "value": ms / args.steps, "unit": "ms/step", "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": False,
+            "config": {"workload": f"learned-closure step kernels, {side}x{side}, untrained network",
+                       "engine": ["tcgen05", "mma.sync"][args.closure_engine]},
+            "avg_launch_ms": {"stage1": avg[0], "stage2": avg[1], "predict": avg[2]},
+            "predict_tflops": flop_eval * side * side / (avg[2] * 1e-3) / 1e12, "gpu_launches": int(sum(launches))}
+
+
 def run_closure(args):
     """Config-5 workload: train the closure on seeded level-4 runs, then time-to-solution at T = 2 on a
     1024^2 held-out member: plain level 4 against level 1 closed by the network (and plain level 1),
@@ -501,12 +541,13 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
-    ap.add_argument("--workload", choices=["grid", "tri", "ensemble", "closure"], default="grid",
+    ap.add_argument("--workload", choices=["grid", "tri", "ensemble", "closure", "closure-kernels"], default="grid",
                     help="grid: the 2048^2 level-2 benchmark (default); tri: the ~4M-triangle level-3 dam break; "
                          "ensemble: 512 ragged level-1 members in one persistent launch; closure: learned "
                          "closure vs level 4, time to T = 2 on 1024^2")
     ap.add_argument("--closure-members", type=int, default=256, help="level-4 training runs (closure workload)")
     ap.add_argument("--closure-train-side", type=int, default=128, help="grid side of the training runs")
+    ap.add_argument("--closure-engine", type=int, default=0, help="closure network engine: 0 tcgen05, 1 mma.sync")
     ap.add_argument("--rows-per-warp", type=int, default=0,
                     help="fixed structured-kernel segment height instead of the autotuner (profiling runs)")
     args = ap.parse_args()
@@ -528,6 +569,8 @@ def main():
         line = run_ensemble(args) if rank == 0 else None
     elif args.workload == "closure":
         line = run_closure(args) if rank == 0 else None
+    elif args.workload == "closure-kernels":
+        line = run_closure_kernels(args) if rank == 0 else None
     else:
         line = run_ours(args, rank, world, local_rank)
     if rank == 0 and line is not None:

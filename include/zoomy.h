@@ -175,9 +175,17 @@ zoomy_status zoomy_closure_set(zoomy_ctx *ctx, const float *params, const float 
                                double lambda);
 zoomy_status zoomy_closure_clear(zoomy_ctx *ctx);
 
-/* The closure MLP alone, with the in-kernel tensor-core code: feat (device, SoA [6][n], unscaled
- * features) -> out (device, SoA [6][n], the six predicted moments).  Queued on the context's stream. */
+/* The closure MLP alone, with the solver's tensor-core code: feat (device, SoA [6][n], unscaled
+ * features) -> out (device, SoA [6][n], the six predicted moments).  Queued on the context's
+ * stream; a tensor-core completion wait that gives up is reported as ZOOMY_ETIMEOUT by the next
+ * synchronising call (zoomy_sync). */
 zoomy_status zoomy_closure_eval(zoomy_ctx *ctx, const float *feat, float *out, int64_t n);
+
+/* Tensor-core engine of the closure network: 0 (default) = tcgen05.mma with FP32 accumulators in
+ * tensor memory, 128 cells per MMA tile; 1 = warp-level mma.sync (m16n8k16).  Both round the
+ * weights and the layer inputs to BF16 and accumulate in FP32; they differ only in the order of
+ * the FP32 accumulation.  EINVAL for other values. */
+zoomy_status zoomy_closure_engine(zoomy_ctx *ctx, int32_t engine);
 
 /* ---- Training the closure MLP ------------------------------------------------------------------
  * Full-batch (or caller-sliced mini-batch) training of the closure network above by hand-written

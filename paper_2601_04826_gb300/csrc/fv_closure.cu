@@ -20,7 +20,9 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include "f32x2.cuh"
 #include "fv_common.cuh"
+#include "tcgen05.cuh"
 #include "zoomy_internal.h"
 #include "zoomy_kernels.h"
 
@@ -365,18 +367,35 @@ __global__ void __launch_bounds__(128) k_stage_closure(ClosureArgs ca)
     }
     float xprev[CL_NV] = {0, 0, 0, 0, 0}, accp[CL_NV] = {0, 0, 0, 0, 0};
     unsigned flag = 0;
-    for (int r = r0 - 1; r <= r1; ++r) {
-        const int rs = r < 0 ? 0 : (r >= a.ny ? a.ny - 1 : r);
-        const bool ywall = (r < 0 && a.bc[2] == 1) || (r >= a.ny && a.bc[3] == 1);
+    // the next row's state, bed and predictions are loaded one iteration ahead
+    float xn[CL_NV], bn, pn[6];
+    auto load_row = [&](int rr) {
+        const int rs = rr < 0 ? 0 : (rr >= a.ny ? a.ny - 1 : rr);
         const int64_t idx = (int64_t)rs * a.nx + csrc;
-        float x[CL_NV];
 #pragma unroll
-        for (int v = 0; v < CL_NV; ++v) x[v] = __ldg(a.X + v * a.ld + idx);
-        const float bed = __ldg(a.bed + idx);
+        for (int v = 0; v < CL_NV; ++v) xn[v] = __ldg(a.X + v * a.ld + idx);
+        bn = __ldg(a.bed + idx);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) pn[j] = __ldg(ca.pred + j * ca.pstride + idx);
+    };
+    load_row(r0 - 1);
+    for (int r = r0 - 1; r <= r1; ++r) {
+        const bool ywall = (r < 0 && a.bc[2] == 1) || (r >= a.ny && a.bc[3] == 1);
+        float x[CL_NV], pred[6];
+#pragma unroll
+        for (int v = 0; v < CL_NV; ++v) x[v] = xn[v];
+        const float bed = bn;
         // closure of this row's cells (predicted from the unreflected state; ghosts reflect it)
-        float pred[6];
 #pragma unroll
-        for (int j = 0; j < 6; ++j) pred[j] = __ldg(ca.pred + j * ca.pstride + idx);
+        for (int j = 0; j < 6; ++j) pred[j] = pn[j];
+        if (r < r1) load_row(r + 1);
+        // Q^n of the row finished in this iteration (stage 2), requested before the face work
+        float qn[CL_NV];
+        if (STAGE == 2) {
+            const int64_t qidx = (int64_t)(r - 1 >= r0 ? r - 1 : r0) * a.nx + csrc;
+#pragma unroll
+            for (int v = 0; v < CL_NV; ++v) qn[v] = __ldg(a.Qn + v * a.ld + qidx);
+        }
         float q[CL_NV];
 #pragma unroll
         for (int v = 0; v < CL_NV; ++v) q[v] = x[v];
@@ -457,7 +476,7 @@ __global__ void __launch_bounds__(128) k_stage_closure(ClosureArgs ca)
                 const int64_t oidx = (int64_t)(r - 1) * a.nx + (owned ? col : csrc);
                 if (STAGE == 2) {
 #pragma unroll
-                    for (int v = 0; v < CL_NV; ++v) y[v] = 0.5f * (a.Qn[v * a.ld + oidx] + y[v]);
+                    for (int v = 0; v < CL_NV; ++v) y[v] = 0.5f * (qn[v] + y[v]);
                     // (the next step's prediction kernel takes the new state's wave speed)
                     if (owned) {
                         bool bad = false;
@@ -564,6 +583,237 @@ __global__ void __launch_bounds__(128) k_closure_eval(const ClosureDev *gnet, co
 }
 
 // ------------------------------------------------------------------------------------------
+// The same network on the 5th-generation tensor cores: a CTA of 4 warps takes 128 cells per tile
+// (cell i of the tile = row i of the MMA = tensor-memory lane i, owned by thread i).  Per layer one
+// thread issues tcgen05.mma (M = 128, N = 64 or 16, K = 16 per instruction) from BF16 operands in
+// shared memory into FP32 accumulators in tensor memory; the threads read their row back with
+// tcgen05.ld, add the bias, apply the GELU and write the BF16 row of the next layer's A operand.
+// Every completion wait is bounded; a wait that gives up raises DEV_TIMEOUT, waits once more for
+// the outstanding MMAs and frees the tensor memory before returning.
+// ------------------------------------------------------------------------------------------
+
+// Weights in the K-major no-swizzle operand layout (B operands are the transposed weights).
+// B3 comes first so that even a mis-read LBO/SBO pair would stay inside the structure.
+struct ClosureTC {
+    uint16_t B3[16 * 64];  // W3^T: 6 outputs (padded to 16) x 64
+    uint16_t B1[64 * 16];  // W1^T: 64 x 6 inputs (padded to 16)
+    uint16_t B2[64 * 64];  // W2^T
+    float b1[64], b2[64], b3[16];
+    float in_scale[8], out_scale[8];
+};
+static_assert(sizeof(ClosureTC) % 16 == 0, "ClosureTC is copied in 16-byte words");
+
+struct TCSmem {
+    ClosureTC net;
+    alignas(128) uint16_t A1[128 * 16];  // layer-1 input tile (K = 16)
+    alignas(128) uint16_t A2[128 * 64];  // layer-2 and layer-3 input tile (K = 64)
+    uint64_t bar;
+    uint32_t tmem;
+};
+
+// One 64-column accumulator region serves the three layers in turn (each layer's accumulator is
+// read back completely before the next MMA is issued), so up to 8 CTAs fit the 512 columns of an
+// SM; registers (256 threads of at most 64) allow 4.
+constexpr uint32_t TC_COLS = 64;
+constexpr long long TC_WAIT = 2000000000LL;    // ~1 s at 2 GHz
+constexpr int TC_DYN_SMEM = 0;
+constexpr int TC_THREADS = 256;
+constexpr int TC_CTAS_PER_SM = 4;
+constexpr uint32_t TC_IDESC64 = tc::idesc_bf16_f32(128, 64);
+constexpr uint32_t TC_IDESC16 = tc::idesc_bf16_f32(128, 16);
+
+// MODE 0: predict from the stage input (ca.s.X) into ca.pred; MODE 1: the same plus the closed wave
+// speed into slot a.slot_out; MODE 2: evaluate feat [6][n] (unscaled features) into out [6][n].
+// 256 threads: tensor-memory lane (row) r = tid % 128 is read by two threads, which take the hidden
+// columns [0, 32) and [32, 64) of every layer (warps w and w + 4 share a lane quarter).  The threads
+// of the first half load the tile's inputs and write its outputs.
+template <int MODE>
+__global__ void __launch_bounds__(TC_THREADS, TC_CTAS_PER_SM) k_closure_tc(ClosureArgs ca, const ClosureTC *gnet,
+                                                                           const float *feat, float *out, int64_t n)
+{
+    __shared__ __align__(1024) TCSmem sm;
+    const StageArgs<float> &a = ca.s;
+    const int tid = threadIdx.x, warp = tid >> 5, row = tid & 127, half = tid >> 7;
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(gnet);
+        uint4 *dst = reinterpret_cast<uint4 *>(&sm.net);
+        for (int i = tid; i < (int)(sizeof(ClosureTC) / 16); i += TC_THREADS) dst[i] = src[i];
+        // columns 8..15 of the layer-1 input are zero padding for every tile
+        if (half == 0) *reinterpret_cast<uint4 *>(&sm.A1[tc::kmajor_index(row, 8, 16)]) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (warp == 0) tc::tmem_alloc(&sm.tmem, TC_COLS);
+    if (tid == 0) tc::mbar_init(&sm.bar, 1);
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = sm.tmem;
+    const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);  // this warp's 32 lanes
+    const bool skip = MODE != 2 && __syncthreads_or(tid == 0 && *(volatile unsigned int *)&a.ctl->status != 0u);
+    const uint32_t sa1 = tc::smem_u32(sm.A1), sa2 = tc::smem_u32(sm.A2);
+    const uint32_t sb1 = tc::smem_u32(sm.net.B1), sb2 = tc::smem_u32(sm.net.B2), sb3 = tc::smem_u32(sm.net.B3);
+    const int64_t nc = MODE == 2 ? n : (int64_t)a.nx * a.ny;
+    const int64_t ntiles = (nc + 127) / 128;
+    uint32_t phase = 0;
+    bool failed = false;
+    float smax = 0.0f;
+    unsigned flag = 0;
+    auto wait = [&]() {
+        const bool ok = tc::mbar_wait(&sm.bar, phase, TC_WAIT);
+        if (__syncthreads_or(!ok)) return false;
+        phase ^= 1u;
+        tc::fence_after_sync();
+        return true;
+    };
+    // bias + GELU of this thread's 32 accumulator columns -> BF16 into its half of the A2 row.  The
+    // two loads are issued back to back and waited for once; the GELU runs on packed FP32 pairs.
+    auto hidden32 = [&](const float *bias) {
+        uint32_t r[32];
+        const int c0 = 32 * half;
+        tc::tmem_ld16_nowait(trow + c0, r);
+        tc::tmem_ld16_nowait(trow + c0 + 16, r + 16);
+        tc::wait_ld();
+        const F2 k0(0.7978845608028654f), k1(0.7978845608028654f * 0.044715f), hf(0.5f);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            uint32_t w[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int j = 8 * g + 2 * q;
+                const F2 z = F2(__uint_as_float(r[j]), __uint_as_float(r[j + 1])) + F2(bias[c0 + j], bias[c0 + j + 1]);
+                const F2 u = z * fma2(k1, z * z, k0);
+                const F2 t(tanh_approx(u.x()), tanh_approx(u.y()));
+                const F2 hz = hf * z;
+                const F2 gz = fma2(hz, t, hz);
+                w[q] = pack_bf16(gz.x(), gz.y());
+            }
+            *reinterpret_cast<uint4 *>(&sm.A2[tc::kmajor_index(row, c0 + 8 * g, 64)]) =
+                make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    };
+    // the next tile's inputs are requested while this tile's layers run (first-half threads)
+    float in_next[6];
+    auto load_in = [&](int64_t tile) {
+        if (half != 0 || tile >= ntiles) return;
+        const int64_t i = tile * 128 + row;
+        const int64_t ic = i < nc ? i : nc - 1;
+#pragma unroll
+        for (int v = 0; v < (MODE == 2 ? 6 : CL_NV); ++v)
+            in_next[v] = MODE == 2 ? __ldg(feat + v * n + ic) : __ldg(a.X + v * a.ld + ic);
+    };
+    load_in(blockIdx.x);
+    for (int64_t tile = blockIdx.x; tile < ntiles && !skip; tile += gridDim.x) {
+        const int64_t i = tile * 128 + row;
+        float x[CL_NV];
+        if (half == 0) {
+            float f[6];
+            if (MODE == 2) {
+#pragma unroll
+                for (int j = 0; j < 6; ++j) f[j] = in_next[j];
+            } else {
+#pragma unroll
+                for (int v = 0; v < CL_NV; ++v) x[v] = in_next[v];
+                features(x, ca.lambda, a.hdry, f);
+            }
+            const float *is = sm.net.in_scale;
+            uint4 w;
+            w.x = pack_bf16(f[0] * is[0], f[1] * is[1]);
+            w.y = pack_bf16(f[2] * is[2], f[3] * is[3]);
+            w.z = pack_bf16(f[4] * is[4], f[5] * is[5]);
+            w.w = 0u;
+            *reinterpret_cast<uint4 *>(&sm.A1[tc::kmajor_index(row, 0, 16)]) = w;
+        }
+        // layer 1: D = A1 (128 x 16) W1
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            tc::mma_bf16(tmem, tc::smem_desc(sa1, 128, 256), tc::smem_desc(sb1, 128, 256), TC_IDESC64, 0u);
+            tc::commit(&sm.bar);
+        }
+        load_in(tile + gridDim.x);
+        if (!wait()) {
+            failed = true;
+            break;
+        }
+        hidden32(sm.net.b1);
+        // layer 2: D = A2 (128 x 64) W2, four K = 16 steps
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                tc::mma_bf16(tmem, tc::smem_desc(sa2 + 256 * k, 128, 1024), tc::smem_desc(sb2 + 256 * k, 128, 1024),
+                             TC_IDESC64, k > 0 ? 1u : 0u);
+            tc::commit(&sm.bar);
+        }
+        if (!wait()) {
+            failed = true;
+            break;
+        }
+        hidden32(sm.net.b2);
+        // layer 3: D[0,16) = A2 (128 x 64) W3 (outputs padded to 16)
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                tc::mma_bf16(tmem, tc::smem_desc(sa2 + 256 * k, 128, 1024), tc::smem_desc(sb3 + 256 * k, 128, 1024),
+                             TC_IDESC16, k > 0 ? 1u : 0u);
+            tc::commit(&sm.bar);
+        }
+        if (!wait()) {
+            failed = true;
+            break;
+        }
+        if (half == 0) {  // warps 0-3 read the output columns of their lane quarter
+            float y[8], p[6];
+            tc::tmem_ld8(trow, y);
+#pragma unroll
+            for (int j = 0; j < 6; ++j) p[j] = (y[j] + sm.net.b3[j]) * sm.net.out_scale[j];
+            if (i < nc) {
+                float *dst = MODE == 2 ? out : ca.pred;
+                const int64_t stride = MODE == 2 ? n : ca.pstride;
+#pragma unroll
+                for (int j = 0; j < 6; ++j) dst[j * stride + i] = p[j];
+            }
+            if (MODE == 1) {
+                CRec r;
+                make_crec(r, x[0], 0.0f, x, p, false, false, a.hdry);
+                const float sp = r.um + sqrtf(a.g * fmaxf(x[0], 0.0f) + r.s2) + r.s1;
+                if (i < nc) {
+                    if (!(sp <= 3.0e38f)) flag |= DEV_NAN;
+                    if (!(x[0] >= 0.0f)) flag |= (x[0] < 0.0f) ? DEV_NEGDEPTH : DEV_NAN;
+                    smax = (sp > smax || sp != sp) ? sp : smax;
+                }
+            }
+        }
+        // every row of D3 is read before the next tile's layer 1 overwrites those columns
+        tc::fence_before_sync();
+        __syncthreads();
+    }
+    if (failed) {
+        if (tid == 0) atomicOr(&a.ctl->status, DEV_TIMEOUT);
+        tc::mbar_wait(&sm.bar, phase, TC_WAIT);  // the MMAs still in flight, once more with a limit
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, TC_COLS);
+    }
+    if (MODE == 1) {
+        if (flag) atomicOr(&a.ctl->status, flag);
+        reduce_smax<float>(a.ctl, a.slot_out, smax);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // Host side
 // ------------------------------------------------------------------------------------------
 
@@ -606,6 +856,46 @@ static void build_closure_dev(const float *p, const float *in_scale, const float
     memcpy(d.out_scale, out_scale, sizeof(float) * 6);
 }
 
+// The network in the tcgen05 operand layout (weights rounded to BF16 like the mma.sync image).
+static void build_closure_tc(const float *p, const float *in_scale, const float *out_scale, ClosureTC &d)
+{
+    const float *W1 = p, *b1 = W1 + 6 * 64, *W2 = b1 + 64, *b2 = W2 + 64 * 64, *W3 = b2 + 64, *b3 = W3 + 64 * 6;
+    memset(&d, 0, sizeof(d));
+    for (int n = 0; n < 64; ++n)
+        for (int k = 0; k < 16; ++k) d.B1[tc::kmajor_index(n, k, 16)] = to_bf16(k < 6 ? W1[k * 64 + n] : 0.0f);
+    for (int n = 0; n < 64; ++n)
+        for (int k = 0; k < 64; ++k) d.B2[tc::kmajor_index(n, k, 64)] = to_bf16(W2[k * 64 + n]);
+    for (int n = 0; n < 16; ++n)
+        for (int k = 0; k < 64; ++k) d.B3[tc::kmajor_index(n, k, 64)] = to_bf16(n < 6 ? W3[k * 6 + n] : 0.0f);
+    memcpy(d.b1, b1, sizeof(float) * 64);
+    memcpy(d.b2, b2, sizeof(float) * 64);
+    for (int j = 0; j < 6; ++j) {
+        d.b3[j] = b3[j];
+        d.in_scale[j] = in_scale[j];
+        d.out_scale[j] = out_scale[j];
+    }
+}
+
+static cudaError_t launch_predict(zoomy_ctx *c, const ClosureArgs &ca, bool ws)
+{
+    if (c->closure_engine == 0) {
+        const unsigned grid = (unsigned)(TC_CTAS_PER_SM * c->nsm);
+        if (ws)
+            k_closure_tc<1><<<grid, TC_THREADS, TC_DYN_SMEM, c->stream>>>(ca, (const ClosureTC *)c->closure_tc, nullptr,
+                                                                   nullptr, 0);
+        else
+            k_closure_tc<0><<<grid, TC_THREADS, TC_DYN_SMEM, c->stream>>>(ca, (const ClosureTC *)c->closure_tc, nullptr,
+                                                                   nullptr, 0);
+    } else {
+        const unsigned pgrid = (unsigned)(4 * c->nsm);
+        if (ws)
+            k_closure_predict<true><<<pgrid, 128, 0, c->stream>>>(ca);
+        else
+            k_closure_predict<false><<<pgrid, 128, 0, c->stream>>>(ca);
+    }
+    return cudaGetLastError();
+}
+
 zoomy_status closure_run_steps(zoomy_ctx *c, float *Q, int64_t ld, double dt, int nsteps)
 {
     ClosureArgs ca;
@@ -638,7 +928,6 @@ zoomy_status closure_run_steps(zoomy_ctx *c, float *Q, int64_t ld, double dt, in
     float *Q1 = (float *)c->q1;
     const int nwarps = a.nstrips * a.nsegs;
     dim3 grid((nwarps + 3) / 4), block(128);
-    const unsigned pgrid = (unsigned)(4 * c->nsm);
     for (int k = 0; k < nsteps; ++k) {
         // closure of Q^n and its wave speed (this step's dt) into slot k & 1, cleared by the previous
         // step's first stage (or at the start of the call)
@@ -646,8 +935,7 @@ zoomy_status closure_run_steps(zoomy_ctx *c, float *Q, int64_t ld, double dt, in
         a.slot_out = k & 1;
         zoomy_status ps = prof_mark(c, 3, true);
         if (ps != ZOOMY_OK) return ps;
-        k_closure_predict<true><<<pgrid, 128, 0, c->stream>>>(ca);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = launch_predict(c, ca, true);
         if (e != cudaSuccess) return cuda_fail(e, "closure prediction launch");
         if ((ps = prof_mark(c, 3, false)) != ZOOMY_OK) return ps;
         a.slot_in = k & 1;
@@ -660,8 +948,7 @@ zoomy_status closure_run_steps(zoomy_ctx *c, float *Q, int64_t ld, double dt, in
         if ((ps = prof_mark(c, 1, false)) != ZOOMY_OK) return ps;
         a.X = Q1;
         if ((ps = prof_mark(c, 3, true)) != ZOOMY_OK) return ps;
-        k_closure_predict<false><<<pgrid, 128, 0, c->stream>>>(ca);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "closure prediction launch");
+        if ((e = launch_predict(c, ca, false)) != cudaSuccess) return cuda_fail(e, "closure prediction launch");
         if ((ps = prof_mark(c, 3, false)) != ZOOMY_OK) return ps;
         a.Qn = Q;
         a.out = Q;
@@ -685,7 +972,14 @@ zoomy_status closure_upload(zoomy_ctx *c, const float *params, const float *in_s
         cudaError_t e = cudaMalloc(&c->closure_pred, sizeof(float) * 6 * (size_t)(c->nx * c->ny));
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
     }
+    if (!c->closure_tc) {
+        cudaError_t e = cudaMalloc(&c->closure_tc, sizeof(ClosureTC));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    }
+    ClosureTC t;
+    build_closure_tc(params, in_scale, out_scale, t);
     cudaError_t e = cudaMemcpy(c->closure_d, &d, sizeof(ClosureDev), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->closure_tc, &t, sizeof(ClosureTC), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
     return ZOOMY_OK;
 }
@@ -700,9 +994,25 @@ extern "C" zoomy_status zoomy_closure_eval(zoomy_ctx *c, const float *feat, floa
     if (!c->closure_d) return set_error(ZOOMY_ESTATE, "zoomy_closure_eval: no closure set");
     if (n == 0) return ZOOMY_OK;
     int64_t blocks = (n + 127) / 128;
-    if (blocks > 8LL * c->nsm) blocks = 8LL * c->nsm;
-    k_closure_eval<<<(unsigned)blocks, 128, 0, c->stream>>>((const ClosureDev *)c->closure_d, feat, out, n);
+    if (c->closure_engine == 0) {
+        if (blocks > (int64_t)TC_CTAS_PER_SM * c->nsm) blocks = (int64_t)TC_CTAS_PER_SM * c->nsm;
+        ClosureArgs ca;
+        memset(&ca, 0, sizeof(ca));
+        ca.s.ctl = c->ctl;  // a timed-out completion wait is reported by the next synchronising call
+        k_closure_tc<2><<<(unsigned)blocks, TC_THREADS, TC_DYN_SMEM, c->stream>>>(ca, (const ClosureTC *)c->closure_tc,
+                                                                         feat, out, n);
+    } else {
+        if (blocks > 8LL * c->nsm) blocks = 8LL * c->nsm;
+        k_closure_eval<<<(unsigned)blocks, 128, 0, c->stream>>>((const ClosureDev *)c->closure_d, feat, out, n);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "closure eval launch");
+    return ZOOMY_OK;
+}
+
+extern "C" zoomy_status zoomy_closure_engine(zoomy_ctx *c, int32_t engine)
+{
+    if (!c || engine < 0 || engine > 1) return set_error(ZOOMY_EINVAL, "zoomy_closure_engine: engine is 0 or 1");
+    c->closure_engine = engine;
     return ZOOMY_OK;
 }

@@ -46,7 +46,6 @@ struct EnsArgs {
     long long spin_limit;   // barrier spin iterations before giving up
 };
 
-enum : unsigned { DEV_TIMEOUT = 8u };
 
 // Arguments of one member for one phase: 0 reads Q; stage 1 reads Q, writes Q1; stage 2 reads Q1 and
 // Q^n = Q, writes Q in place.

@@ -116,6 +116,7 @@ extern "C" zoomy_status zoomy_mesh_destroy(zoomy_ctx *c)
     cudaFree(c->qdev_host);
     cudaFree(c->closure_d);
     cudaFree(c->closure_pred);
+    cudaFree(c->closure_tc);
     for (cudaEvent_t ev : c->prof_events) cudaEventDestroy(ev);
     tri_free(c);
     ens_free(c);
@@ -300,6 +301,7 @@ zoomy_status zoomy::read_status(zoomy_ctx *c, double *t_total)
     if (h.status & DEV_NAN) return set_error(ZOOMY_ENAN, "a step produced a non-finite state");
     if (h.status & DEV_NEGDEPTH) return set_error(ZOOMY_ENEGDEPTH, "a step produced a negative depth");
     if (h.status & DEV_NOWAVE) return set_error(ZOOMY_ECFL, "no positive finite wave speed for the CFL step");
+    if (h.status & DEV_TIMEOUT) return set_error(ZOOMY_ETIMEOUT, "a device-side wait exceeded its limit");
     return ZOOMY_OK;
 }
 

@@ -50,6 +50,8 @@ struct zoomy_ctx {
     // learned closure (fv_closure.cu): level-1 model closed with predicted level-4 moments
     void *closure_d = nullptr;
     void *closure_pred = nullptr;  // predicted closed moments of the current stage input [6][nx ny]
+    void *closure_tc = nullptr;    // the network in the tcgen05 operand layout
+    int closure_engine = 0;        // 0: tcgen05 (tensor memory), 1: mma.sync
     bool closure_on = false;
     double closure_lambda = 0.0;
     // ensemble (fv_ensemble.cu)
@@ -61,6 +63,10 @@ struct zoomy_ctx {
 };
 
 namespace zoomy {
+// Status bit of a device-side wait that gave up (ensemble grid barrier, tensor-core completion
+// waits); the other bits (DEV_NAN, DEV_NEGDEPTH, DEV_NOWAVE) are in fv_common.cuh.
+enum : unsigned int { DEV_TIMEOUT = 8u };
+
 // Segment height of the structured 2D row-marching kernels when none was set: about
 // warps_per_sm warps per SM over the grid (30-column strips), within [8, 64] rows.
 inline int rows_per_warp_for(int64_t nx, int64_t ny, int nsm, int warps_per_sm)

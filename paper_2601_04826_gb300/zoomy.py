@@ -66,6 +66,7 @@ _SIGNATURES = [
     ("zoomy_closure_set", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double]),
     ("zoomy_closure_clear", C.c_int, [C.c_void_p]),
     ("zoomy_closure_eval", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]),
+    ("zoomy_closure_engine", C.c_int, [C.c_void_p, C.c_int32]),
     ("zoomy_mlp_create", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
     ("zoomy_mlp_destroy", C.c_int, [C.c_void_p]),
     ("zoomy_mlp_get_params", C.c_int, [C.c_void_p, C.c_void_p]),
@@ -236,6 +237,10 @@ def zoomy_closure_clear(ctx):
 
 def zoomy_closure_eval(ctx, feat, out, n):
     _check(lib().zoomy_closure_eval(ctx, _ptr(feat), _ptr(out), n))
+
+
+def zoomy_closure_engine(ctx, engine):
+    _check(lib().zoomy_closure_engine(ctx, engine))
 
 
 def zoomy_mlp_create(params, stream=None):

@@ -30,10 +30,14 @@ def Z():
     return zoomy
 
 
-def run_closure(Z, oracle, params, ins, outs, nx, ny, nsteps, Q0, bed, C=0.1, nu=0.01, bc=(1, 0, 1, 1)):
+ENGINES = [0, 1]  # tcgen05 (tensor memory), mma.sync
+
+
+def run_closure(Z, oracle, params, ins, outs, nx, ny, nsteps, Q0, bed, C=0.1, nu=0.01, bc=(1, 0, 1, 1), engine=0):
     Q0r, bedr = rounded(Q0, 0), rounded(bed, 0)
     ctx = Z.Context(Z.mesh_2d(nx, ny, bc=bc, bathymetry=bedr), 1, Z.friction(1, C=C, nu=nu), dtype=0)
     Z.zoomy_closure_set(ctx.ctx, params, ins, outs, C)
+    Z.zoomy_closure_engine(ctx.ctx, engine)
     Q = to_device(Q0r, 0)
     tg = ctx.step(Q, nsteps=nsteps, dt=0.0)
     got = Q.double().cpu().numpy()
@@ -55,10 +59,12 @@ def state(nx, ny, seed):
     return Q0, bed
 
 
-def test_zero_network_is_level1(Z, oracle):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_zero_network_is_level1(Z, oracle, engine):
     nx, ny = 95, 67
     Q0, bed = state(nx, ny, 1)
-    got, ref, tg, tr = run_closure(Z, oracle, np.zeros(mlp.NPARAMS), np.ones(6), np.ones(6), nx, ny, 20, Q0, bed)
+    got, ref, tg, tr = run_closure(Z, oracle, np.zeros(mlp.NPARAMS), np.ones(6), np.ones(6), nx, ny, 20, Q0, bed,
+                                   engine=engine)
     assert np.all(rel_l1(got, ref) <= 1e-5), rel_l1(got, ref)
     m1 = oracle.Model(1, 2, g=G, h_dry=1e-6, friction=1, C=0.1, nu=0.01)
     ref1, _ = oracle.step(m1, oracle.Mesh.rect(nx, ny, 0, 1, 0, 1, bc=(1, 0, 1, 1)), rounded(Q0, 0), 20,
@@ -66,18 +72,21 @@ def test_zero_network_is_level1(Z, oracle):
     assert np.all(rel_l1(got, ref1) <= 1e-5)
 
 
-def test_constant_closure_fv_parity(Z, oracle):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_constant_closure_fv_parity(Z, oracle, engine):
     nx, ny = 88, 61
     Q0, bed = state(nx, ny, 3)
     p = {k: np.zeros_like(v) for k, v in mlp.init_params(0).items()}
     p["b3"] = np.array([0.125, -0.0625, 0.03125, -0.09375, 0.046875, -0.015625])  # exact in BF16/FP32
-    got, ref, tg, tr = run_closure(Z, oracle, mlp.pack(p), np.ones(6), np.ones(6), nx, ny, 20, Q0, bed)
+    got, ref, tg, tr = run_closure(Z, oracle, mlp.pack(p), np.ones(6), np.ones(6), nx, ny, 20, Q0, bed,
+                                   engine=engine)
     err = rel_l1(got, ref)
     assert np.all(err <= 1e-5), err
     assert tg == pytest.approx(tr, rel=1e-5)
 
 
-def test_mlp_eval_matches_oracle(Z, oracle):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_mlp_eval_matches_oracle(Z, oracle, engine):
     import torch
 
     rng = np.random.default_rng(2)
@@ -89,13 +98,14 @@ def test_mlp_eval_matches_oracle(Z, oracle):
     nx = ny = 16
     ctx = Z.Context(Z.mesh_2d(nx, ny), 1, Z.friction(1, C=0.1, nu=0.01), dtype=0)
     Z.zoomy_closure_set(ctx.ctx, mlp.pack(p), ins, outs, 0.1)
+    Z.zoomy_closure_engine(ctx.ctx, engine)
     n = 3001
     F = np.stack([rng.uniform(0.5, 1.5, n), rng.uniform(-0.5, 0.5, n), rng.uniform(-0.5, 0.5, n),
                   rng.uniform(-0.3, 0.3, n), rng.uniform(-0.3, 0.3, n), rng.uniform(0.05, 0.3, n)])
     Fd = torch.tensor(F, dtype=torch.float32, device="cuda")
     Od = torch.zeros_like(Fd)
     Z.zoomy_closure_eval(ctx.ctx, Fd, Od, n)
-    torch.cuda.synchronize()
+    Z.zoomy_sync(ctx.ctx)
     got = Od.double().cpu().numpy().T
     ctx.close()
     p32 = mlp.unpack(np.asarray(mlp.pack(p), dtype=np.float32).astype(np.float64))
@@ -108,7 +118,8 @@ def test_mlp_eval_matches_oracle(Z, oracle):
     assert rel < 2e-2 and cos > 0.999, (rel, cos)
 
 
-def test_random_network_closed_solver(Z, oracle):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_random_network_closed_solver(Z, oracle, engine):
     nx, ny = 70, 52
     Q0, bed = state(nx, ny, 5)
     rng = np.random.default_rng(11)
@@ -117,7 +128,36 @@ def test_random_network_closed_solver(Z, oracle):
         p[k] = 0.5 * p[k] + 0.02 * rng.normal(size=p[k].shape)
     ins = np.array([1.0, 2.0, 2.0, 4.0, 4.0, 5.0])
     outs = np.full(6, 0.05)
-    got, ref, tg, tr = run_closure(Z, oracle, mlp.pack(p), ins, outs, nx, ny, 10, Q0, bed)
+    got, ref, tg, tr = run_closure(Z, oracle, mlp.pack(p), ins, outs, nx, ny, 10, Q0, bed, engine=engine)
     err = rel_l1(got, ref)
-    print("closed solver relative L1", err)
+    print("closed solver relative L1", engine, err)
     assert np.all(err <= 1e-4), err
+
+
+def test_engines_agree(Z):
+    """tcgen05 and mma.sync evaluate the same BF16 network: they differ only in the FP32 accumulation
+    order (and the BF16 rounding of a layer input that lands on the other side of a tie)."""
+    import torch
+
+    rng = np.random.default_rng(12)
+    p = mlp.init_params(3)
+    ins = np.array([1.0, 2.0, 2.0, 4.0, 4.0, 5.0])
+    outs = np.full(6, 0.1)
+    ctx = Z.Context(Z.mesh_2d(8, 8), 1, Z.friction(1, C=0.1, nu=0.01), dtype=0)
+    Z.zoomy_closure_set(ctx.ctx, mlp.pack(p), ins, outs, 0.1)
+    n = 128 * 37 + 51  # several tiles per CTA and a ragged last tile
+    F = torch.tensor(np.stack([rng.uniform(0.5, 1.5, n), rng.uniform(-0.5, 0.5, n), rng.uniform(-0.5, 0.5, n),
+                               rng.uniform(-0.3, 0.3, n), rng.uniform(-0.3, 0.3, n), rng.uniform(0.05, 0.3, n)]),
+                     dtype=torch.float32, device="cuda")
+    outs_ = []
+    for engine in ENGINES:
+        Z.zoomy_closure_engine(ctx.ctx, engine)
+        O = torch.full_like(F, float("nan"))
+        Z.zoomy_closure_eval(ctx.ctx, F, O, n)
+        Z.zoomy_sync(ctx.ctx)
+        outs_.append(O.double().cpu().numpy())
+    ctx.close()
+    a, b = outs_
+    assert np.all(np.isfinite(a)) and np.all(np.isfinite(b))
+    rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+    assert rel < 2e-3, rel
