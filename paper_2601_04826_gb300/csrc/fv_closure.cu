@@ -594,212 +594,233 @@ __global__ void __launch_bounds__(128) k_closure_eval(const ClosureDev *gnet, co
 
 // Weights in the K-major no-swizzle operand layout (B operands are the transposed weights).
 // B3 comes first so that even a mis-read LBO/SBO pair would stay inside the structure.
+// The biases ride on the tensor core: columns 6 and 7 of every layer-1 input row hold 1.0, and
+// the matching columns of B1 / Bb2 / Bb3 hold the bias split into two BF16 parts (hi + lo, ~16
+// bits), so a K = 16 step with the layer-1 tile as A adds the bias of layers 2 and 3.  Layers 1
+// and 2 are scaled by 1/2 (exact in BF16): the accumulator holds z/2, and the GELU
+// z/2 (1 + tanh(c (z + 0.044715 z^3))) is evaluated in terms of z/2.
 struct ClosureTC {
-    uint16_t B3[16 * 64];  // W3^T: 6 outputs (padded to 16) x 64
-    uint16_t B1[64 * 16];  // W1^T: 64 x 6 inputs (padded to 16)
-    uint16_t B2[64 * 64];  // W2^T
-    float b1[64], b2[64], b3[16];
+    uint16_t B3[16 * 64];   // W3^T: 6 outputs (padded to 16) x 64
+    uint16_t Bb3[16 * 16];  // b3 in columns 6, 7
+    uint16_t B1[64 * 16];   // W1^T / 2 (6 inputs, padded to 16), b1 / 2 in columns 6, 7
+    uint16_t B2[64 * 64];   // W2^T / 2
+    uint16_t Bb2[64 * 16];  // b2 / 2 in columns 6, 7
     float in_scale[8], out_scale[8];
 };
 static_assert(sizeof(ClosureTC) % 16 == 0, "ClosureTC is copied in 16-byte words");
 
 struct TCSmem {
     ClosureTC net;
-    alignas(128) uint16_t A1[128 * 16];  // layer-1 input tile (K = 16)
-    alignas(128) uint16_t A2[128 * 64];  // layer-2 and layer-3 input tile (K = 64)
-    uint64_t bar;
+    alignas(128) uint16_t A1[2][128 * 16];  // layer-1 input tiles (K = 16), one per tile in flight
+    alignas(128) uint16_t A2[2][128 * 64];  // layer-2 and layer-3 input tiles (K = 64)
+    uint64_t bar[2];
     uint32_t tmem;
 };
 
-// One 64-column accumulator region serves the three layers in turn (each layer's accumulator is
-// read back completely before the next MMA is issued), so up to 8 CTAs fit the 512 columns of an
-// SM; registers (256 threads of at most 64) allow 4.
-constexpr uint32_t TC_COLS = 64;
+// Two tiles are in flight per CTA: while the tensor core runs one tile's layer, the threads apply
+// the GELU to the other tile's previous layer.  Each tile owns a 64-column accumulator region that
+// serves its three layers in turn (a layer's accumulator is read back completely before the next
+// MMA into it is issued): 128 columns per CTA, 4 CTAs per SM (53 KB of shared memory each).
+constexpr uint32_t TC_COLS = 128;
 constexpr long long TC_WAIT = 2000000000LL;    // ~1 s at 2 GHz
-constexpr int TC_DYN_SMEM = 0;
-constexpr int TC_THREADS = 256;
+constexpr int TC_DYN_SMEM = (int)sizeof(TCSmem);
+constexpr int TC_THREADS = 128;
 constexpr int TC_CTAS_PER_SM = 4;
 constexpr uint32_t TC_IDESC64 = tc::idesc_bf16_f32(128, 64);
 constexpr uint32_t TC_IDESC16 = tc::idesc_bf16_f32(128, 16);
 
 // MODE 0: predict from the stage input (ca.s.X) into ca.pred; MODE 1: the same plus the closed wave
 // speed into slot a.slot_out; MODE 2: evaluate feat [6][n] (unscaled features) into out [6][n].
-// 256 threads: tensor-memory lane (row) r = tid % 128 is read by two threads, which take the hidden
-// columns [0, 32) and [32, 64) of every layer (warps w and w + 4 share a lane quarter).  The threads
-// of the first half load the tile's inputs and write its outputs.
+// Thread r owns row r of both tiles in flight (tensor-memory lane r).
 template <int MODE>
 __global__ void __launch_bounds__(TC_THREADS, TC_CTAS_PER_SM) k_closure_tc(ClosureArgs ca, const ClosureTC *gnet,
                                                                            const float *feat, float *out, int64_t n)
 {
-    __shared__ __align__(1024) TCSmem sm;
+    extern __shared__ __align__(1024) uint8_t tc_smem[];  // sizeof(TCSmem) bytes (above the static limit)
+    TCSmem &sm = *reinterpret_cast<TCSmem *>(tc_smem);
     const StageArgs<float> &a = ca.s;
-    const int tid = threadIdx.x, warp = tid >> 5, row = tid & 127, half = tid >> 7;
+    const int tid = threadIdx.x, warp = tid >> 5;
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(gnet);
         uint4 *dst = reinterpret_cast<uint4 *>(&sm.net);
         for (int i = tid; i < (int)(sizeof(ClosureTC) / 16); i += TC_THREADS) dst[i] = src[i];
-        // columns 8..15 of the layer-1 input are zero padding for every tile
-        if (half == 0) *reinterpret_cast<uint4 *>(&sm.A1[tc::kmajor_index(row, 8, 16)]) = make_uint4(0u, 0u, 0u, 0u);
+        // columns 8..15 of the layer-1 inputs are zero padding for every tile
+        *reinterpret_cast<uint4 *>(&sm.A1[0][tc::kmajor_index(tid, 8, 16)]) = make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4 *>(&sm.A1[1][tc::kmajor_index(tid, 8, 16)]) = make_uint4(0u, 0u, 0u, 0u);
     }
     if (warp == 0) tc::tmem_alloc(&sm.tmem, TC_COLS);
-    if (tid == 0) tc::mbar_init(&sm.bar, 1);
+    if (tid == 0) {
+        tc::mbar_init(&sm.bar[0], 1);
+        tc::mbar_init(&sm.bar[1], 1);
+    }
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = sm.tmem;
-    const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);  // this warp's 32 lanes
+    const uint32_t tlane = (uint32_t)(warp * 32) << 16;  // this warp's 32 lanes
     const bool skip = MODE != 2 && __syncthreads_or(tid == 0 && *(volatile unsigned int *)&a.ctl->status != 0u);
-    const uint32_t sa1 = tc::smem_u32(sm.A1), sa2 = tc::smem_u32(sm.A2);
     const uint32_t sb1 = tc::smem_u32(sm.net.B1), sb2 = tc::smem_u32(sm.net.B2), sb3 = tc::smem_u32(sm.net.B3);
+    const uint32_t sbb2 = tc::smem_u32(sm.net.Bb2), sbb3 = tc::smem_u32(sm.net.Bb3);
     const int64_t nc = MODE == 2 ? n : (int64_t)a.nx * a.ny;
     const int64_t ntiles = (nc + 127) / 128;
-    uint32_t phase = 0;
+    uint32_t phase[2] = {0u, 0u};
     bool failed = false;
     float smax = 0.0f;
     unsigned flag = 0;
-    auto wait = [&]() {
-        const bool ok = tc::mbar_wait(&sm.bar, phase, TC_WAIT);
+    float x[2][CL_NV];  // the stage input of this thread's cells (wave speed)
+
+    auto load = [&](int64_t tile, float *dst) {
+        const int64_t i = tile * 128 + tid;
+        const int64_t ic = i < nc ? i : nc - 1;
+#pragma unroll
+        for (int v = 0; v < (MODE == 2 ? 6 : CL_NV); ++v)
+            dst[v] = MODE == 2 ? __ldg(feat + v * n + ic) : __ldg(a.X + v * a.ld + ic);
+    };
+    // features of this thread's cell -> BF16 row of the layer-1 tile b
+    auto prep = [&](int b, const float *in) {
+        float f[6];
+        if (MODE == 2) {
+#pragma unroll
+            for (int j = 0; j < 6; ++j) f[j] = in[j];
+        } else {
+#pragma unroll
+            for (int v = 0; v < CL_NV; ++v) x[b][v] = in[v];
+            features(x[b], ca.lambda, a.hdry, f);
+        }
+        const float *is = sm.net.in_scale;
+        uint4 w;
+        w.x = pack_bf16(f[0] * is[0], f[1] * is[1]);
+        w.y = pack_bf16(f[2] * is[2], f[3] * is[3]);
+        w.z = pack_bf16(f[4] * is[4], f[5] * is[5]);
+        w.w = 0x3F803F80u;  // 1.0, 1.0: the bias columns
+        *reinterpret_cast<uint4 *>(&sm.A1[b][tc::kmajor_index(tid, 0, 16)]) = w;
+    };
+    // the operand tiles written by all threads -> the tensor core; then one thread issues layer L of tile b
+    auto issue = [&](int b, int L) {
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t d = tmem + 64 * b;
+            const uint32_t sa1 = tc::smem_u32(sm.A1[b]), sa2 = tc::smem_u32(sm.A2[b]);
+            if (L == 1) {
+                tc::mma_bf16(d, tc::smem_desc(sa1, 128, 256), tc::smem_desc(sb1, 128, 256), TC_IDESC64, 0u);
+            } else {
+                // the bias (layer-1 tile's ones columns x Bb), then the four K = 16 steps of the layer
+                const uint32_t sb = L == 2 ? sb2 : sb3, idesc = L == 2 ? TC_IDESC64 : TC_IDESC16;
+                tc::mma_bf16(d, tc::smem_desc(sa1, 128, 256), tc::smem_desc(L == 2 ? sbb2 : sbb3, 128, 256), idesc, 0u);
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    tc::mma_bf16(d, tc::smem_desc(sa2 + 256 * k, 128, 1024), tc::smem_desc(sb + 256 * k, 128, 1024),
+                                 idesc, 1u);
+            }
+            tc::commit(&sm.bar[b]);
+        }
+    };
+    auto wait = [&](int b) {
+        const bool ok = tc::mbar_wait(&sm.bar[b], phase[b], TC_WAIT);
         if (__syncthreads_or(!ok)) return false;
-        phase ^= 1u;
+        phase[b] ^= 1u;
         tc::fence_after_sync();
         return true;
     };
-    // bias + GELU of this thread's 32 accumulator columns -> BF16 into its half of the A2 row.  The
-    // two loads are issued back to back and waited for once; the GELU runs on packed FP32 pairs.
-    auto hidden32 = [&](const float *bias) {
-        uint32_t r[32];
-        const int c0 = 32 * half;
-        tc::tmem_ld16_nowait(trow + c0, r);
-        tc::tmem_ld16_nowait(trow + c0 + 16, r + 16);
-        tc::wait_ld();
-        const F2 k0(0.7978845608028654f), k1(0.7978845608028654f * 0.044715f), hf(0.5f);
+    // GELU of the 64 accumulator columns of tile b (which hold z/2, bias included) -> BF16 row of its
+    // A2 tile.  The four loads are issued back to back and waited for once; with h = z/2,
+    // GELU(z) = h (1 + tanh(h (2c + 8 * 0.044715 c h^2))), evaluated on packed FP32 pairs.
+    auto hidden = [&](int b) {
+        uint32_t r[64];
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
+        for (int c = 0; c < 4; ++c) tc::tmem_ld16_nowait(tmem + tlane + 64 * b + 16 * c, r + 16 * c);
+        tc::wait_ld();
+        const F2 kb(2.0f * 0.7978845608028654f), ka(8.0f * 0.044715f * 0.7978845608028654f);
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
             uint32_t w[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int j = 8 * g + 2 * q;
-                const F2 z = F2(__uint_as_float(r[j]), __uint_as_float(r[j + 1])) + F2(bias[c0 + j], bias[c0 + j + 1]);
-                const F2 u = z * fma2(k1, z * z, k0);
+                const F2 h(__uint_as_float(r[j]), __uint_as_float(r[j + 1]));
+                const F2 u = h * fma2(ka, h * h, kb);
                 const F2 t(tanh_approx(u.x()), tanh_approx(u.y()));
-                const F2 hz = hf * z;
-                const F2 gz = fma2(hz, t, hz);
+                const F2 gz = fma2(h, t, h);
                 w[q] = pack_bf16(gz.x(), gz.y());
             }
-            *reinterpret_cast<uint4 *>(&sm.A2[tc::kmajor_index(row, c0 + 8 * g, 64)]) =
-                make_uint4(w[0], w[1], w[2], w[3]);
+            *reinterpret_cast<uint4 *>(&sm.A2[b][tc::kmajor_index(tid, 8 * g, 64)]) = make_uint4(w[0], w[1], w[2], w[3]);
         }
     };
-    // the next tile's inputs are requested while this tile's layers run (first-half threads)
-    float in_next[6];
-    auto load_in = [&](int64_t tile) {
-        if (half != 0 || tile >= ntiles) return;
-        const int64_t i = tile * 128 + row;
-        const int64_t ic = i < nc ? i : nc - 1;
+    // layer-3 accumulator of tile b -> outputs of this thread's cell
+    auto output = [&](int b, int64_t tile) {
+        float y[8], p[6];
+        tc::tmem_ld8(tmem + tlane + 64 * b, y);
 #pragma unroll
-        for (int v = 0; v < (MODE == 2 ? 6 : CL_NV); ++v)
-            in_next[v] = MODE == 2 ? __ldg(feat + v * n + ic) : __ldg(a.X + v * a.ld + ic);
-    };
-    load_in(blockIdx.x);
-    for (int64_t tile = blockIdx.x; tile < ntiles && !skip; tile += gridDim.x) {
-        const int64_t i = tile * 128 + row;
-        float x[CL_NV];
-        if (half == 0) {
-            float f[6];
-            if (MODE == 2) {
+        for (int j = 0; j < 6; ++j) p[j] = y[j] * sm.net.out_scale[j];
+        const int64_t i = tile * 128 + tid;
+        if (i < nc) {
+            float *dst = MODE == 2 ? out : ca.pred;
+            const int64_t stride = MODE == 2 ? n : ca.pstride;
 #pragma unroll
-                for (int j = 0; j < 6; ++j) f[j] = in_next[j];
-            } else {
-#pragma unroll
-                for (int v = 0; v < CL_NV; ++v) x[v] = in_next[v];
-                features(x, ca.lambda, a.hdry, f);
-            }
-            const float *is = sm.net.in_scale;
-            uint4 w;
-            w.x = pack_bf16(f[0] * is[0], f[1] * is[1]);
-            w.y = pack_bf16(f[2] * is[2], f[3] * is[3]);
-            w.z = pack_bf16(f[4] * is[4], f[5] * is[5]);
-            w.w = 0u;
-            *reinterpret_cast<uint4 *>(&sm.A1[tc::kmajor_index(row, 0, 16)]) = w;
+            for (int j = 0; j < 6; ++j) dst[j * stride + i] = p[j];
         }
-        // layer 1: D = A1 (128 x 16) W1
-        tc::fence_async_smem();
-        tc::fence_before_sync();
-        __syncthreads();
-        if (tid == 0) {
-            tc::fence_after_sync();
-            tc::mma_bf16(tmem, tc::smem_desc(sa1, 128, 256), tc::smem_desc(sb1, 128, 256), TC_IDESC64, 0u);
-            tc::commit(&sm.bar);
-        }
-        load_in(tile + gridDim.x);
-        if (!wait()) {
-            failed = true;
-            break;
-        }
-        hidden32(sm.net.b1);
-        // layer 2: D = A2 (128 x 64) W2, four K = 16 steps
-        tc::fence_async_smem();
-        tc::fence_before_sync();
-        __syncthreads();
-        if (tid == 0) {
-            tc::fence_after_sync();
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                tc::mma_bf16(tmem, tc::smem_desc(sa2 + 256 * k, 128, 1024), tc::smem_desc(sb2 + 256 * k, 128, 1024),
-                             TC_IDESC64, k > 0 ? 1u : 0u);
-            tc::commit(&sm.bar);
-        }
-        if (!wait()) {
-            failed = true;
-            break;
-        }
-        hidden32(sm.net.b2);
-        // layer 3: D[0,16) = A2 (128 x 64) W3 (outputs padded to 16)
-        tc::fence_async_smem();
-        tc::fence_before_sync();
-        __syncthreads();
-        if (tid == 0) {
-            tc::fence_after_sync();
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                tc::mma_bf16(tmem, tc::smem_desc(sa2 + 256 * k, 128, 1024), tc::smem_desc(sb3 + 256 * k, 128, 1024),
-                             TC_IDESC16, k > 0 ? 1u : 0u);
-            tc::commit(&sm.bar);
-        }
-        if (!wait()) {
-            failed = true;
-            break;
-        }
-        if (half == 0) {  // warps 0-3 read the output columns of their lane quarter
-            float y[8], p[6];
-            tc::tmem_ld8(trow, y);
-#pragma unroll
-            for (int j = 0; j < 6; ++j) p[j] = (y[j] + sm.net.b3[j]) * sm.net.out_scale[j];
+        if (MODE == 1) {
+            CRec r;
+            make_crec(r, x[b][0], 0.0f, x[b], p, false, false, a.hdry);
+            const float sp = r.um + sqrtf(a.g * fmaxf(x[b][0], 0.0f) + r.s2) + r.s1;
             if (i < nc) {
-                float *dst = MODE == 2 ? out : ca.pred;
-                const int64_t stride = MODE == 2 ? n : ca.pstride;
-#pragma unroll
-                for (int j = 0; j < 6; ++j) dst[j * stride + i] = p[j];
-            }
-            if (MODE == 1) {
-                CRec r;
-                make_crec(r, x[0], 0.0f, x, p, false, false, a.hdry);
-                const float sp = r.um + sqrtf(a.g * fmaxf(x[0], 0.0f) + r.s2) + r.s1;
-                if (i < nc) {
-                    if (!(sp <= 3.0e38f)) flag |= DEV_NAN;
-                    if (!(x[0] >= 0.0f)) flag |= (x[0] < 0.0f) ? DEV_NEGDEPTH : DEV_NAN;
-                    smax = (sp > smax || sp != sp) ? sp : smax;
-                }
+                if (!(sp <= 3.0e38f)) flag |= DEV_NAN;
+                if (!(x[b][0] >= 0.0f)) flag |= (x[b][0] < 0.0f) ? DEV_NEGDEPTH : DEV_NAN;
+                smax = (sp > smax || sp != sp) ? sp : smax;
             }
         }
-        // every row of D3 is read before the next tile's layer 1 overwrites those columns
+    };
+
+    float inA[6], inB[6];
+    const int64_t npairs = (ntiles + 1) / 2;
+    if (!skip && blockIdx.x < npairs) load(2 * blockIdx.x, inA);
+    for (int64_t pr = blockIdx.x; pr < npairs && !skip; pr += gridDim.x) {
+        const int64_t tA = 2 * pr, tB = 2 * pr + 1;
+        const bool hasB = tB < ntiles;  // uniform across the CTA
+        if (hasB) load(tB, inB);
+        prep(0, inA);
+        issue(0, 1);
+        if (hasB) {
+            prep(1, inB);
+            issue(1, 1);
+        }
+        if (pr + gridDim.x < npairs) load(2 * (pr + gridDim.x), inA);  // next pair's first tile
+        // layer 1 -> 2 -> 3 of both tiles, each epilogue overlapping the other tile's MMA
+        if (!wait(0)) { failed = true; break; }
+        hidden(0);
+        issue(0, 2);
+        if (hasB) {
+            if (!wait(1)) { failed = true; break; }
+            hidden(1);
+            issue(1, 2);
+        }
+        if (!wait(0)) { failed = true; break; }
+        hidden(0);
+        issue(0, 3);
+        if (hasB) {
+            if (!wait(1)) { failed = true; break; }
+            hidden(1);
+            issue(1, 3);
+        }
+        if (!wait(0)) { failed = true; break; }
+        output(0, tA);
+        if (hasB) {
+            if (!wait(1)) { failed = true; break; }
+            output(1, tB);
+        }
+        // every accumulator row is read before the next pair's layer-1 MMAs overwrite the regions
         tc::fence_before_sync();
         __syncthreads();
     }
     if (failed) {
         if (tid == 0) atomicOr(&a.ctl->status, DEV_TIMEOUT);
-        tc::mbar_wait(&sm.bar, phase, TC_WAIT);  // the MMAs still in flight, once more with a limit
+        // the MMAs still in flight, once more with a limit
+        tc::mbar_wait(&sm.bar[0], phase[0], TC_WAIT);
+        tc::mbar_wait(&sm.bar[1], phase[1], TC_WAIT);
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -857,20 +878,35 @@ static void build_closure_dev(const float *p, const float *in_scale, const float
 }
 
 // The network in the tcgen05 operand layout (weights rounded to BF16 like the mma.sync image).
+static float from_bf16(uint16_t h)
+{
+    const uint32_t u = (uint32_t)h << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
 static void build_closure_tc(const float *p, const float *in_scale, const float *out_scale, ClosureTC &d)
 {
     const float *W1 = p, *b1 = W1 + 6 * 64, *W2 = b1 + 64, *b2 = W2 + 64 * 64, *W3 = b2 + 64, *b3 = W3 + 64 * 6;
     memset(&d, 0, sizeof(d));
-    for (int n = 0; n < 64; ++n)
-        for (int k = 0; k < 16; ++k) d.B1[tc::kmajor_index(n, k, 16)] = to_bf16(k < 6 ? W1[k * 64 + n] : 0.0f);
-    for (int n = 0; n < 64; ++n)
-        for (int k = 0; k < 64; ++k) d.B2[tc::kmajor_index(n, k, 64)] = to_bf16(W2[k * 64 + n]);
-    for (int n = 0; n < 16; ++n)
-        for (int k = 0; k < 64; ++k) d.B3[tc::kmajor_index(n, k, 64)] = to_bf16(n < 6 ? W3[k * 6 + n] : 0.0f);
-    memcpy(d.b1, b1, sizeof(float) * 64);
-    memcpy(d.b2, b2, sizeof(float) * 64);
+    // a bias value as two BF16 parts in columns 6 (hi) and 7 (lo) of a K = 16 row
+    auto bias = [&](uint16_t *B, int n, float v) {
+        const uint16_t hi = to_bf16(v);
+        B[tc::kmajor_index(n, 6, 16)] = hi;
+        B[tc::kmajor_index(n, 7, 16)] = to_bf16(v - from_bf16(hi));
+    };
+    for (int n = 0; n < 64; ++n) {
+        for (int k = 0; k < 6; ++k) d.B1[tc::kmajor_index(n, k, 16)] = to_bf16(0.5f * W1[k * 64 + n]);
+        bias(d.B1, n, 0.5f * b1[n]);
+        for (int k = 0; k < 64; ++k) d.B2[tc::kmajor_index(n, k, 64)] = to_bf16(0.5f * W2[k * 64 + n]);
+        bias(d.Bb2, n, 0.5f * b2[n]);
+    }
+    for (int n = 0; n < 6; ++n) {
+        for (int k = 0; k < 64; ++k) d.B3[tc::kmajor_index(n, k, 64)] = to_bf16(W3[k * 6 + n]);
+        bias(d.Bb3, n, b3[n]);
+    }
     for (int j = 0; j < 6; ++j) {
-        d.b3[j] = b3[j];
         d.in_scale[j] = in_scale[j];
         d.out_scale[j] = out_scale[j];
     }
@@ -975,6 +1011,14 @@ zoomy_status closure_upload(zoomy_ctx *c, const float *params, const float *in_s
     if (!c->closure_tc) {
         cudaError_t e = cudaMalloc(&c->closure_tc, sizeof(ClosureTC));
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+        // the two-tile operand buffers exceed the default 48 KB of shared memory per CTA
+        if ((e = cudaFuncSetAttribute(k_closure_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_DYN_SMEM)) !=
+                cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_closure_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_DYN_SMEM)) !=
+                cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_closure_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_DYN_SMEM)) !=
+                cudaSuccess)
+            return cuda_fail(e, "cudaFuncSetAttribute");
     }
     ClosureTC t;
     build_closure_tc(params, in_scale, out_scale, t);
