@@ -265,7 +265,7 @@ def run_tri(args):
 
     build.build()
     level, nv = 3, 9
-    verts, tris = inputs.jittered_delaunay(1415, seed=0)
+    verts, tris = inputs.jittered_delaunay(args.tri_side, seed=0)
     Q0 = inputs.circular_dam_tri(verts, tris, level, radius=0.2, h_in=1.5)
     nc = len(tris)
     ctx = zoomy.Context(zoomy.mesh_tri(verts, tris, bc=1), level, zoomy.friction(2, manning_n=0.03), dtype=0)
@@ -546,6 +546,8 @@ def main():
                          "ensemble: 512 ragged level-1 members in one persistent launch; closure: learned "
                          "closure vs level 4, time to T = 2 on 1024^2")
     ap.add_argument("--closure-members", type=int, default=256, help="level-4 training runs (closure workload)")
+    ap.add_argument("--tri-side", type=int, default=1415,
+                    help="lattice side of the triangle workload (1415: ~4M triangles; smaller for profiling runs)")
     ap.add_argument("--closure-train-side", type=int, default=128, help="grid side of the training runs")
     ap.add_argument("--closure-engine", type=int, default=0, help="closure network engine: 0 tcgen05, 1 mma.sync")
     ap.add_argument("--rows-per-warp", type=int, default=0,

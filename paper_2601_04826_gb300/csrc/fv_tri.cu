@@ -189,6 +189,7 @@ struct TriArgs {
     const float *geo;        // nx[3][nc], ny[3][nc], |e|/|Omega| [3][nc]
     int64_t nc;
     int wall;                // boundary edges: 1 wall, 0 transmissive
+    int nsm;                 // SMs of the device (grid size)
 };
 
 template <int N>
@@ -230,28 +231,37 @@ __global__ void __launch_bounds__(128) k_stage_tri(TriArgs a)
         return;
     }
     if (STAGE == 1 && blockIdx.x == 0 && threadIdx.x == 0) step_bookkeeping(s, dt);
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     float smax = 0.0f;
     unsigned flag = 0;
-    if (i < a.nc) {
+    // grid-stride over the cells: a bounded grid keeps the wave-speed reduction at one atomic per CTA
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.nc; i += (int64_t)gridDim.x * blockDim.x) {
+        // every load of the cell is issued up front: its state, the neighbour indices, the face
+        // geometry, the three neighbours' states (gathers) and, in stage 2, Q^n
         float raw[nv + 1];
         tri_load<N>(a, i, raw);
+        int32_t jn[3];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) jn[f] = __ldg(a.nbr + f * a.nc + i);
+        float qn[nv];
+        if (STAGE == 2) {
+#pragma unroll
+            for (int v = 0; v < nv; ++v) qn[v] = __ldg(s.Qn + v * s.ld + i);
+        }
+        float rawn[3][nv + 1];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) tri_load<N>(a, jn[f] >= 0 ? jn[f] : i, rawn[f]);
         float acc[nv];
 #pragma unroll
         for (int v = 0; v < nv; ++v) acc[v] = 0.0f;
+#pragma unroll
         for (int f = 0; f < 3; ++f) {
-            const int32_t j = __ldg(a.nbr + f * a.nc + i);
+            const int32_t j = jn[f];
             const float nx = __ldg(a.geo + f * a.nc + i), ny = __ldg(a.geo + (3 + f) * a.nc + i);
             const float lw = __ldg(a.geo + (6 + f) * a.nc + i);
             CellRec<N, 2, float> L, R;
             tri_cell<N>(raw, nx, ny, false, s.hdry, L);
-            if (j >= 0) {
-                float rawj[nv + 1];
-                tri_load<N>(a, j, rawj);
-                tri_cell<N>(rawj, nx, ny, false, s.hdry, R);
-            } else {
-                tri_cell<N>(raw, nx, ny, a.wall != 0, s.hdry, R);  // ghost: copy or wall reflection
-            }
+            // neighbour, or the ghost of a boundary face: copy or wall reflection of this cell
+            tri_cell<N>(rawn[f], nx, ny, j < 0 && a.wall != 0, s.hdry, R);
             float fc[1 + 2 * m], nc[1 + 2 * m], pd;
             face_term<N, 2, float>(L, frame<N, 2, float, false>(L), R, frame<N, 2, float, false>(R), s.g, s.hdry, fc,
                                    pd, nc);
@@ -293,7 +303,7 @@ __global__ void __launch_bounds__(128) k_stage_tri(TriArgs a)
         }
         if (STAGE == 2) {
 #pragma unroll
-            for (int v = 0; v < nv; ++v) y[v] = 0.5f * (s.Qn[v * s.ld + i] + y[v]);
+            for (int v = 0; v < nv; ++v) y[v] = 0.5f * (qn[v] + y[v]);
             CellRec<N, 2, float> co;
 #pragma unroll
             for (int k = 0; k < m; ++k) {
@@ -304,21 +314,35 @@ __global__ void __launch_bounds__(128) k_stage_tri(TriArgs a)
             const float sp = wavespeed<N, 2, float>(co, s.g);
             if (!(sp <= 3.0e38f)) flag |= DEV_NAN;
             if (!(y[0] >= 0.0f)) flag |= (y[0] < 0.0f) ? DEV_NEGDEPTH : DEV_NAN;
-            smax = sp;
+            smax = (sp > smax || sp != sp) ? sp : smax;
         }
 #pragma unroll
         for (int v = 0; v < nv; ++v) s.out[v * s.ld + i] = y[v];
     }
     if (STAGE == 2) {
         if (flag) atomicOr(&s.ctl->status, flag);
-        reduce_smax<float>(s.ctl, s.slot_out, smax);
+        // block maximum (NaN wins), then one atomic per CTA
+        __shared__ float wmax[4];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float v = __shfl_xor_sync(0xffffffffu, smax, o);
+            smax = (v > smax || v != v) ? v : smax;
+        }
+        if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = smax;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            smax = threadIdx.x < 4 ? wmax[threadIdx.x] : 0.0f;
+            reduce_smax<float>(s.ctl, s.slot_out, smax);
+        }
     }
 }
 
 template <int N>
 static cudaError_t launch_tri(const TriArgs &a, int stage, cudaStream_t st)
 {
-    dim3 grid((unsigned)((a.nc + 127) / 128)), block(128);
+    int64_t blocks = (a.nc + 127) / 128;
+    if (blocks > (int64_t)a.nsm * 16) blocks = (int64_t)a.nsm * 16;
+    dim3 grid((unsigned)(blocks > 0 ? blocks : 1)), block(128);
     if (stage == 1)
         k_stage_tri<N, 1><<<grid, block, 0, st>>>(a);
     else
@@ -359,6 +383,7 @@ zoomy_status tri_run_steps(zoomy_ctx *c, float *Q, int64_t ld, double dt, int ns
     a.geo = c->tri_geo_d;
     a.nc = c->nc;
     a.wall = c->bc[0] == ZOOMY_BC_WALL;
+    a.nsm = c->nsm;
     float *Q1 = (float *)c->q1;
     for (int k = 0; k < nsteps; ++k) {
         s.slot_in = k & 1;
