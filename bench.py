@@ -41,20 +41,25 @@ KERNEL_SOURCES = ["paper_2601_04826_gb300/csrc/fv_struct2d_f32.cu", "paper_2601_
                   "paper_2601_04826_gb300/csrc/basis.cuh"]
 
 
-def kernel_hash():
+TRI_KERNEL_SOURCES = ["paper_2601_04826_gb300/csrc/fv_tri.cu", "paper_2601_04826_gb300/csrc/model.cuh",
+                      "paper_2601_04826_gb300/csrc/fv_common.cuh", "paper_2601_04826_gb300/csrc/basis.cuh"]
+
+
+def kernel_hash(sources=None):
     h = hashlib.sha256()
-    for p in KERNEL_SOURCES:
+    for p in sources or KERNEL_SOURCES:
         with open(os.path.join(ROOT, p), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:12]
 
 
-def ncu_traffic():
-    """DRAM bytes per stage-2 launch from the committed ncu summary, if it was taken on this kernel source."""
+def ncu_traffic(sources=None):
+    """DRAM bytes per launch of the dominant kernel from a committed ncu summary, if it was taken on the
+    current source of that kernel (the summary line carries a hash of the kernel's source files)."""
     d = os.path.join(ROOT, "profiles")
     if not os.path.isdir(d):
         return None
-    want = kernel_hash()
+    want = kernel_hash(sources)
     for fn in sorted(os.listdir(d)):
         if not fn.endswith((".md", ".txt")):
             continue
@@ -298,7 +303,8 @@ def run_tri(args):
             "config": {"workload": "2D shallow-moment level 3 on a jittered-point Delaunay triangle mesh "
                                    f"({nc} cells, Morton order), Manning n=0.03, dry outside a circular dam, walls"},
             "roofline": {"bound": "hbm", "kernel": "k_stage_tri<3,2>", "achieved": ach, "peak": hbm,
-                         "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / hbm,
+                         "traffic": ncu_traffic(TRI_KERNEL_SOURCES) if args.tri_side == 1415 else None,
                          "algorithmic_bytes_per_launch": b2 * nc,
                          "avg_launch_ms": {"stage1": kms[0] / max(launches[0], 1), "stage2": avg2}},
             "gpu_launches": int(launches[0] + launches[1] + 1), "clocks": clk.summary()}
