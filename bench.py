@@ -148,6 +148,23 @@ def workload():
     return Q0, b
 
 
+def max_over_ranks(x, world, device):
+    """The maximum of a per-rank float over all ranks (the slowest replica times the job)."""
+    if world <= 1:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, steps, seconds_max, world):
+    """Whole-job throughput of independent replicas: the units all ranks advanced over the slowest
+    rank's time (weak scaling: every rank advances the same workload)."""
+    return world * units_per_rank * steps / seconds_max
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -192,11 +209,7 @@ def run_ours(args, rank, world, local_rank):
     t_sim = zoomy.zoomy_sync(ctx.ctx)  # raises on a device-detected error
     launches, kms = zoomy.zoomy_profile_read(ctx.ctx)
     zoomy.zoomy_profile_enable(ctx.ctx, False)
-    ms = e0.elapsed_time(e1)
-    ms_t = torch.tensor([ms], device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms = float(ms_t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
 
     # end-to-end through the host-buffer entry point: H2D of the state, one step, D2H of the result
     e2e_s = float("nan")
@@ -208,11 +221,7 @@ def run_ours(args, rank, world, local_rank):
         t0 = time.perf_counter()
         for _ in range(n_e2e):
             ctx.step_host(Qh, nsteps=1, dt=0.0)
-        e2e_s = (time.perf_counter() - t0) / n_e2e
-        e2e_t = torch.tensor([e2e_s], device=dev)
-        if world > 1:
-            torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(e2e_t.item())
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / n_e2e, world, dev)
     ctx.close()
 
     if rank != 0:
@@ -224,7 +233,7 @@ def run_ours(args, rank, world, local_rank):
     avg = avg2 if dom == 2 else avg1
     achieved = BYTES_STAGE[dom] * nc / (avg * 1e-3) / 1e9
     traffic = ncu_traffic() if dom == 2 else None
-    value = world * nc * args.steps / (ms * 1e-3)
+    value = job_throughput(nc, args.steps, ms * 1e-3, world)
     step_bytes = (BYTES_STAGE[1] + BYTES_STAGE[2]) * nc
     line = {
         "metric": METRIC,
@@ -250,7 +259,7 @@ def run_ours(args, rank, world, local_rank):
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
                      "algorithmic_bytes_per_launch": BYTES_STAGE[dom] * nc,
                      "avg_launch_ms": {"stage1": avg1, "stage2": avg2}},
-        "e2e": None if args.no_e2e else {"value": nc / e2e_s * world, "unit": "cell-updates/s",
+        "e2e": None if args.no_e2e else {"value": job_throughput(nc, 1, e2e_s, world), "unit": "cell-updates/s",
                                          "h2d_bytes_per_step": 4 * NV * nc, "d2h_bytes_per_step": 4 * NV * nc},
         "gpu_launches": int(launches[0] + launches[1] + 1),
         "clocks": clk.summary(),
@@ -471,6 +480,40 @@ def run_closure(args):
             "gpu_launches": int(cl_["launches"]), "clocks": clk.summary()}
 
 
+def run_dambreak1d(args):
+    """The 1D dam break (2000 cells, level 1, FP64, slip + Newtonian, transmissive): a latency-bound
+    case (the whole state is 48 KB), reported as time per step.  Prints its own JSON line."""
+    import torch
+
+    from paper_2601_04826_gb300 import build, inputs, zoomy
+
+    build.build()
+    nx, level = 2000, 1
+    Q0 = inputs.dambreak_1d(nx, 0.0, 10.0, h_left=2.0, h_right=1.0, x_dam=5.0, level=level)
+    ctx = zoomy.Context(zoomy.mesh_1d(nx, 0.0, 10.0, bc=(0, 0)), level,
+                        zoomy.friction(zoomy.FRICTION_SLIP_NEWTONIAN, C=0.1, nu=0.01), cfl=0.45, dtype=zoomy.FP64)
+    Q = torch.tensor(Q0, dtype=torch.float64, device="cuda")
+    ctx.step(Q, nsteps=args.warmup, dt=0.0)
+    Q.copy_(torch.tensor(Q0, dtype=torch.float64))
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ctx.step(Q, nsteps=args.steps, dt=0.0, sync=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = zoomy.zoomy_sync(ctx.ctx)
+    ms = e0.elapsed_time(e1)
+    ctx.close()
+    return {"metric": "time per SSP-RK2 step", "value": 1e3 * ms / args.steps, "unit": "us/step",
+            "cell_updates_per_s": nx * args.steps / (ms * 1e-3), "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "1D shallow-moment level 1 dam break, 2000 cells on [0,10], h = 2 / 1, slip "
+                                   "C=0.1 + Newtonian nu=0.01, transmissive, adaptive CFL 0.45",
+                       "sim_time_advanced": t},
+            "gpu_launches": 2 * args.steps + 1}
+
+
 def oracle_window_run(side, nsteps):
     """The oracle on a side x side window of the workload (cells of the 2048^2 grid, walls)."""
     import numpy as np
@@ -547,7 +590,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
-    ap.add_argument("--workload", choices=["grid", "tri", "ensemble", "closure", "closure-kernels"], default="grid",
+    ap.add_argument("--workload", choices=["grid", "tri", "ensemble", "closure", "closure-kernels", "dambreak1d"],
+                    default="grid",
                     help="grid: the 2048^2 level-2 benchmark (default); tri: the ~4M-triangle level-3 dam break; "
                          "ensemble: 512 ragged level-1 members in one persistent launch; closure: learned "
                          "closure vs level 4, time to T = 2 on 1024^2")
@@ -579,6 +623,8 @@ def main():
         line = run_closure(args) if rank == 0 else None
     elif args.workload == "closure-kernels":
         line = run_closure_kernels(args) if rank == 0 else None
+    elif args.workload == "dambreak1d":
+        line = run_dambreak1d(args) if rank == 0 else None
     else:
         line = run_ours(args, rank, world, local_rank)
     if rank == 0 and line is not None:
