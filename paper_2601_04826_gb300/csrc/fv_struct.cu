@@ -287,7 +287,10 @@ __global__ void __launch_bounds__(128) k_stage_2d(StageArgs<T> a)
 template <int N, typename T>
 static cudaError_t launch_1d(const StageArgs<T> &a, int stage, cudaStream_t st)
 {
-    dim3 grid((a.nx + 255) / 256), block(256);
+    // small lines (the work is FP64-rate bound, not memory bound): one-warp CTAs spread the cells
+    // over as many SMs as possible; large lines use 256-thread CTAs
+    const int bs = a.nx < 65536 ? 32 : 256;
+    dim3 grid((a.nx + bs - 1) / bs), block(bs);
     if (stage == 1)
         k_stage_1d<N, T, 1><<<grid, block, 0, st>>>(a);
     else
