@@ -78,6 +78,7 @@ def _declare(L):
     L.or_mesh_2d.restype = vp
     L.or_mesh_tri.argtypes = [C.c_int64, _dp, C.c_int64, _ip32, C.c_int]
     L.or_mesh_tri.restype = vp
+    L.or_lift3d.argtypes = [vp, vp, _dp, vp, C.c_int, _dp, _dp]
     L.or_mesh_free.argtypes = [vp]
     L.or_mesh_ncells.argtypes = [vp]
     L.or_mesh_ncells.restype = C.c_int64
@@ -252,6 +253,17 @@ def cfl_dt(model, mesh, Q, cfl):
 
 def mass(mesh, Q):
     return lib().or_mass(mesh._p, np.ascontiguousarray(Q, dtype=np.float64))
+
+
+def lift3d(model, mesh, Q, zeta, bed=None):
+    """Three-dimensional fields at sigma levels zeta (Sec. "Postprocessing", interpolate_3d):
+    returns [4, K, nc] = u, v, w, p (see or_lift3d)."""
+    Qc = np.ascontiguousarray(Q, dtype=np.float64)
+    z = np.ascontiguousarray(zeta, dtype=np.float64)
+    out = np.zeros((4, len(z), Qc.shape[1]))
+    b, bp = _bed_ptr(bed)
+    lib().or_lift3d(model._p, mesh._p, Qc, bp, len(z), z, out)
+    return out
 
 
 def max_level():

@@ -701,6 +701,70 @@ double or_mass(const or_mesh *me, const double *Q)
 int or_max_level(void) { return OR_MAXN; }
 
 /* ------------------------------------------------------------------------- */
+/* Lifting to three-dimensional fields (Sec. "Postprocessing": interpolate_3d) */
+/* ------------------------------------------------------------------------- */
+
+/* Reading R16.  At sigma levels zeta_j in [0,1] (elevation z = b + zeta h):
+ *   u(zeta) = sum_k alpha_k phi_k(zeta),  v(zeta) = sum_k beta_k phi_k(zeta)   (the moment expansion);
+ *   w(zeta) from continuity, integrated upwards from the bed where w = u.grad b:
+ *     w = -d_x(int_b^z u dz') - d_y(int_b^z v dz')  at fixed z, with int_b^z u dz' = sum_k hA_k Phi_k(zeta),
+ *     so w(zeta) = -sum_k [d_x hA_k + d_y hB_k] Phi_k(zeta) + u(zeta)(d_x b + zeta d_x h)
+ *                  + v(zeta)(d_y b + zeta d_y h);
+ *   p(zeta) = g h (1 - zeta)   (hydrostatic, rho = 1).
+ * Level 0 on a flat bed at zeta = 1 gives the paper's SWE lifting w = -h (d_x u + d_y v).
+ * Horizontal derivatives: Green-Gauss over the cell's faces, face value (q_i + q_j)/2 with q_j = q_i on
+ * boundary faces.  Dry cells (h <= h_dry): u = v = w = 0.  bed may be NULL (flat).
+ * out: [4][K][nc] = u, v, w, p. */
+void or_lift3d(const or_model *md, const or_mesh *me, const double *Q, const double *bed, int K,
+               const double *zeta, double *out)
+{
+    const int64_t nc = me->nc;
+    const int m = md->m, nv = md->nv;
+    for (int64_t i = 0; i < nc; ++i) {
+        double gx[OR_MAXV + 1], gy[OR_MAXV + 1]; /* d/dx, d/dy of every variable and (index nv) of b */
+        for (int v = 0; v <= nv; ++v) gx[v] = gy[v] = 0.0;
+        for (int f = 0; f < me->nf; ++f) {
+            const int64_t j = me->nbr[i * me->nf + f];
+            const double wx = me->flen[i * me->nf + f] * me->fnx[i * me->nf + f];
+            const double wy = me->flen[i * me->nf + f] * me->fny[i * me->nf + f];
+            for (int v = 0; v <= nv; ++v) {
+                const double qi = v < nv ? Q[v * nc + i] : (bed ? bed[i] : 0.0);
+                const double qj = j < 0 ? qi : (v < nv ? Q[v * nc + j] : (bed ? bed[j] : 0.0));
+                const double fv = 0.5 * (qi + qj);
+                gx[v] += wx * fv;
+                gy[v] += wy * fv;
+            }
+        }
+        for (int v = 0; v <= nv; ++v) {
+            gx[v] /= me->area[i];
+            gy[v] /= me->area[i];
+        }
+        double q[OR_MAXV], al[OR_MAXM], be[OR_MAXM];
+        for (int v = 0; v < nv; ++v) q[v] = Q[v * nc + i];
+        velocities(md, q, al, be);
+        const double h = q[0];
+        const int wet = h > md->h_dry;
+        for (int jz = 0; jz < K; ++jz) {
+            double phi[OR_MAXM], dphi[OR_MAXM], Phi[OR_MAXM];
+            basis_eval(md->N, zeta[jz], phi, dphi, Phi);
+            double u = 0.0, v = 0.0, G = 0.0;
+            for (int k = 0; k < m; ++k) {
+                u += al[k] * phi[k];
+                v += be[k] * phi[k];
+                G += gx[ia(md, k)] * Phi[k];
+                if (md->dim == 2) G += gy[ib(md, k)] * Phi[k];
+            }
+            double w = -G + u * (gx[nv] + zeta[jz] * gx[0]) + v * (gy[nv] + zeta[jz] * gy[0]);
+            if (!wet) u = v = w = 0.0;
+            out[(0 * K + jz) * nc + i] = u;
+            out[(1 * K + jz) * nc + i] = v;
+            out[(2 * K + jz) * nc + i] = w;
+            out[(3 * K + jz) * nc + i] = md->g * h * (1.0 - zeta[jz]);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
 /* Learned closure (level-1 prognostic state, level-4 model)                  */
 /* ------------------------------------------------------------------------- */
 /*

@@ -34,10 +34,13 @@ MUTANTS = {
     "tri_normal_y_flipped": ("me->fny[t * 3 + f] = -ex / len;", "me->fny[t * 3 + f] = ex / len;"),
     "tri_edge_length_unit": ("me->flen[t * 3 + f] = len;", "me->flen[t * 3 + f] = 1.0;"),
     "tri_area_doubled": ("me->area[t] = sa;", "me->area[t] = 2.0 * sa;"),
+    "lift_w_sign": ("double w = -G + u * (gx[nv]", "double w = G + u * (gx[nv]"),
+    "lift_depth_gradient_unscaled": ("u * (gx[nv] + zeta[jz] * gx[0])", "u * (gx[nv] + gx[0])"),
+    "lift_phi_for_Phi": ("G += gx[ia(md, k)] * Phi[k];", "G += gx[ia(md, k)] * phi[k];"),
 }
 
 PIN_TESTS = ["tests/test_oracle_basis.py", "tests/test_oracle_model.py", "tests/test_oracle_scheme.py",
-             "tests/test_oracle_triangles.py"]
+             "tests/test_oracle_triangles.py", "tests/test_oracle_lift.py"]
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
