@@ -514,6 +514,49 @@ def run_dambreak1d(args):
             "gpu_launches": 2 * args.steps + 1}
 
 
+def run_lift(args):
+    """Lifting of the 2048^2 level-2 bench state to K = 16 sigma levels (u, v, w, p: 1.07 GB written per
+    launch).  Prints its own JSON line."""
+    import numpy as np
+    import torch
+
+    from paper_2601_04826_gb300 import build, zoomy
+
+    build.build()
+    Q0, b = workload()
+    nc, K = N_SIDE * N_SIDE, 16
+    fr = zoomy.friction(FRIC["kind"], C=FRIC["C"], nu=FRIC["nu"])
+    ctx = zoomy.Context(zoomy.mesh_2d(N_SIDE, N_SIDE, bathymetry=b), LEVEL, fr, cfl=CFL, dtype=zoomy.FP32)
+    Q = torch.tensor(Q0, dtype=torch.float32, device="cuda")
+    ctx.step(Q, nsteps=50, dt=0.0)  # a state with moving water
+    zeta = (np.arange(K) + 0.5) / K
+    out = torch.empty((4 * K, nc), dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        zoomy.zoomy_lift3d(ctx.ctx, Q, nc, zeta, out, nc)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            zoomy.zoomy_lift3d(ctx.ctx, Q, nc, zeta, out, nc)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    ctx.close()
+    hbm, peak_kind = peaks()
+    per_cell = 4 * (NV + 1) + 4 * 4 * K  # state + bed read once, four fields at K levels written
+    ach = per_cell * nc / (ms * 1e-3) / 1e9
+    return {"metric": "lifted cells/s", "value": nc / (ms * 1e-3), "unit": "cells/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (bench state after 50 steps)",
+            "config": {"workload": f"lifting of the 2048x2048 level-2 state to u, v, w, p at {K} sigma levels"},
+            "roofline": {"bound": "hbm", "kernel": "k_lift3d<2,1,float>", "achieved": ach, "peak": hbm,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+                         "algorithmic_bytes_per_launch": per_cell * nc},
+            "gpu_launches": args.steps, "clocks": clk.summary()}
+
+
 def oracle_window_run(side, nsteps):
     """The oracle on a side x side window of the workload (cells of the 2048^2 grid, walls)."""
     import numpy as np
@@ -590,7 +633,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
-    ap.add_argument("--workload", choices=["grid", "tri", "ensemble", "closure", "closure-kernels", "dambreak1d"],
+    ap.add_argument("--workload", choices=["grid", "tri", "ensemble", "closure", "closure-kernels", "dambreak1d",
+                                           "lift"],
                     default="grid",
                     help="grid: the 2048^2 level-2 benchmark (default); tri: the ~4M-triangle level-3 dam break; "
                          "ensemble: 512 ragged level-1 members in one persistent launch; closure: learned "
@@ -625,6 +669,8 @@ def main():
         line = run_closure_kernels(args) if rank == 0 else None
     elif args.workload == "dambreak1d":
         line = run_dambreak1d(args) if rank == 0 else None
+    elif args.workload == "lift":
+        line = run_lift(args) if rank == 0 else None
     else:
         line = run_ours(args, rank, world, local_rank)
     if rank == 0 and line is not None:

@@ -220,6 +220,22 @@ zoomy_status zoomy_closure_samples(const float *Q, int64_t ld, int32_t level, co
                                    double lambda, double h_dry, const float *in_scale, const float *out_scale,
                                    float *X, float *T, void *stream);
 
+/* ---- Lifting to three-dimensional fields ---------------------------------------------------------
+ * The paper's interpolate_3d postprocessing (Sec. "Postprocessing"): from the state Q (device,
+ * [nv][ld], the context's dtype and cell order) the fields u, v, w, p at the K sigma levels zeta[j]
+ * (host, in [0, 1]; elevation z = b + zeta h) of every cell:
+ *   u = sum_k alpha_k phi_k(zeta), v = sum_k beta_k phi_k(zeta)   (the moment expansion),
+ *   w = -sum_k [d_x(h alpha_k) + d_y(h beta_k)] Phi_k(zeta) + u (d_x b + zeta d_x h) + v (d_y b + zeta d_y h)
+ *       (continuity integrated from the bed, where w = u . grad b),
+ *   p = g h (1 - zeta)   (hydrostatic, rho = 1);
+ * horizontal derivatives by Green-Gauss with face values (q_i + q_j)/2 (q_j = q_i on boundary
+ * faces); u = v = w = 0 in dry cells.  out (device, the context's dtype): plane (f, j) of field
+ * f in (u, v, w, p) at out + (f K + j) ldo, ldo >= ncells.  1 <= K <= 64.  Any mesh kind, any
+ * level; queued on the context's stream (no synchronisation).  EINVAL on bad arguments or zeta
+ * outside [0, 1]. */
+zoomy_status zoomy_lift3d(zoomy_ctx *ctx, const void *Q, int64_t ld, int32_t K, const double *zeta, void *out,
+                          int64_t ldo);
+
 /* ---- Batched ensembles (independent runs of uneven sizes in one launch) -------------------------
  * nmembers square grids of side sides[m] on the unit square with walls, each with its own slip
  * coefficient C[m] (Navier slip, rho = 1) and the Newtonian viscosity nu, level `level`, FP32
