@@ -64,6 +64,8 @@ def _declare(L):
                                C.c_double, C.c_double, C.c_double]
     L.or_model_new.restype = vp
     L.or_model_free.argtypes = [vp]
+    L.or_model_set_source_mode.argtypes = [vp, C.c_int]
+    L.or_friction_implicit.argtypes = [vp, _dp, C.c_double]
     L.or_model_nv.argtypes = [vp]
     L.or_flux.argtypes = [vp, _dp, C.c_double, C.c_double, _dp]
     L.or_nc_matrix.argtypes = [vp, _dp, C.c_double, C.c_double, _dp]
@@ -130,11 +132,14 @@ FRICTION_NONE, FRICTION_SLIP_NEWTONIAN, FRICTION_MANNING = 0, 1, 2
 class Model:
     """Level-N shallow-moment model in 1D or 2D (variable order documented in the C file)."""
 
-    def __init__(self, N, dim, g=9.81, h_dry=1e-6, friction=0, C=0.0, nu=0.0, rho=1.0, manning_n=0.0):
+    def __init__(self, N, dim, g=9.81, h_dry=1e-6, friction=0, C=0.0, nu=0.0, rho=1.0, manning_n=0.0,
+                 implicit_source=False):
         self.N, self.dim = N, dim
         self._p = lib().or_model_new(N, dim, g, h_dry, friction, C, nu, rho, manning_n)
         if not self._p:
             raise ValueError("bad model parameters")
+        # reading R17: friction (Newtonian + bottom stress) by backward Euler after each stage
+        lib().or_model_set_source_mode(self._p, 1 if implicit_source else 0)
         self.nv = lib().or_model_nv(self._p)
         self.g, self.h_dry = g, h_dry
 
@@ -164,6 +169,11 @@ class Model:
     def bottom_friction(self, y, dt):
         y = np.array(y, dtype=np.float64)
         lib().or_bottom_friction(self._p, y, dt)
+        return y
+
+    def friction_implicit(self, y, dt):
+        y = np.array(y, dtype=np.float64)
+        lib().or_friction_implicit(self._p, y, dt)
         return y
 
     def index_alpha(self, k):

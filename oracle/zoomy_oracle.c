@@ -166,6 +166,7 @@ typedef struct {
     double B[OR_MAXM * OR_MAXM * OR_MAXM];
     double Cm[OR_MAXM * OR_MAXM];
     double phi0[OR_MAXM];
+    int src_implicit; /* 0: reading R5 (explicit Newtonian, implicit bottom stress); 1: R17 */
 } or_model;
 
 /* Variable order.  1D: (h, hA_0..hA_N).  2D: (h, hA_0, hB_0, hA_1..hA_N, hB_1..hB_N),
@@ -200,6 +201,7 @@ or_model *or_model_new(int N, int dim, double g, double h_dry, int fric, double 
     return md;
 }
 void or_model_free(or_model *md) { free(md); }
+void or_model_set_source_mode(or_model *md, int mode) { md->src_implicit = mode; }
 int or_model_nv(const or_model *md) { return md->nv; }
 
 /* Velocity moments alpha_k = hA_k / h, beta_k = hB_k / h; zero where h <= h_dry (R8). */
@@ -593,6 +595,71 @@ static void face_term(const or_model *md, const double *qi, double bi, const dou
 }
 
 /* One explicit stage Y = R(X + dt L(X)) (readings R5, R6). */
+/* Friction fully implicit (reading R17, the paper's step_source_implicit for Eq. (PDE-source)):
+ * backward Euler on dy/dt = -K y for the moment rows y_k = h alpha_k (and h beta_k), with
+ *   K_ki = (phi_k(0)/M_k) c phi_i(0) + (nu / (rho h^2)) C_ik / M_k,
+ * the bottom stress (c = C/(rho h), or Manning's g n^2 |u_b| / h^(4/3)) and the Newtonian bulk
+ * stress (slip + Newtonian only), h and c frozen at the input y.  (I + dt K) z = y is solved by
+ * Gaussian elimination with partial pivoting; then the dry cut (R8), in place. */
+void or_friction_implicit(const or_model *md, double *y, double dt)
+{
+    double h = y[0];
+    int m = md->m;
+    if (!(h > md->h_dry)) {
+        for (int v = 1; v < md->nv; ++v) y[v] = 0.0;
+        return;
+    }
+    if (md->fric == 0) return;
+    double sa = 0.0, sb = 0.0;
+    for (int k = 0; k < m; ++k) {
+        sa += md->phi0[k] * y[ia(md, k)];
+        if (md->dim == 2) sb += md->phi0[k] * y[ib(md, k)];
+    }
+    double c;
+    if (md->fric == 1) {
+        c = md->C / (md->rho * h);
+    } else {
+        double ub = sa / h, vb = sb / h;
+        c = md->g * md->manning_n * md->manning_n * sqrt(ub * ub + vb * vb) / pow(h, 4.0 / 3.0);
+    }
+    double nuh = md->fric == 1 ? md->nu / (md->rho * h * h) : 0.0;
+    double A[OR_MAXM][OR_MAXM + 2]; /* augmented: two right-hand sides (alpha rows, beta rows) */
+    for (int k = 0; k < m; ++k) {
+        for (int i = 0; i < m; ++i)
+            A[k][i] = (k == i ? 1.0 : 0.0) +
+                      dt * (md->phi0[k] / md->M[k] * c * md->phi0[i] + nuh * md->Cm[i * m + k] / md->M[k]);
+        A[k][m] = y[ia(md, k)];
+        A[k][m + 1] = md->dim == 2 ? y[ib(md, k)] : 0.0;
+    }
+    for (int col = 0; col < m; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < m; ++r)
+            if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+        if (piv != col)
+            for (int j = 0; j < m + 2; ++j) {
+                double t = A[col][j];
+                A[col][j] = A[piv][j];
+                A[piv][j] = t;
+            }
+        for (int r = col + 1; r < m; ++r) {
+            double f = A[r][col] / A[col][col];
+            for (int j = col; j < m + 2; ++j) A[r][j] -= f * A[col][j];
+        }
+    }
+    for (int rhs = 0; rhs < 2; ++rhs) {
+        double z[OR_MAXM];
+        for (int k = m - 1; k >= 0; --k) {
+            double s = A[k][m + rhs];
+            for (int j = k + 1; j < m; ++j) s -= A[k][j] * z[j];
+            z[k] = s / A[k][k];
+        }
+        for (int k = 0; k < m; ++k) {
+            if (rhs == 0) y[ia(md, k)] = z[k];
+            else if (md->dim == 2) y[ib(md, k)] = z[k];
+        }
+    }
+}
+
 void or_stage(const or_model *md, const or_mesh *me, const double *X, const double *bed, double dt,
               double *Y)
 {
@@ -618,9 +685,14 @@ void or_stage(const or_model *md, const or_mesh *me, const double *X, const doub
             face_term(md, qi, bi, qj, bj, nx, ny, term);
             for (int v = 0; v < nv; ++v) acc[v] += me->flen[e] * term[v];
         }
-        or_source_newtonian(md, qi, S);
-        for (int v = 0; v < nv; ++v) y[v] = qi[v] - dt / me->area[i] * acc[v] + dt * S[v];
-        or_bottom_friction(md, y, dt);
+        if (md->src_implicit) {
+            for (int v = 0; v < nv; ++v) y[v] = qi[v] - dt / me->area[i] * acc[v];
+            or_friction_implicit(md, y, dt);
+        } else {
+            or_source_newtonian(md, qi, S);
+            for (int v = 0; v < nv; ++v) y[v] = qi[v] - dt / me->area[i] * acc[v] + dt * S[v];
+            or_bottom_friction(md, y, dt);
+        }
         for (int v = 0; v < nv; ++v) Y[(int64_t)v * nc + i] = y[v];
     }
 }

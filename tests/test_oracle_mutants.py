@@ -37,10 +37,12 @@ MUTANTS = {
     "lift_w_sign": ("double w = -G + u * (gx[nv]", "double w = G + u * (gx[nv]"),
     "lift_depth_gradient_unscaled": ("u * (gx[nv] + zeta[jz] * gx[0])", "u * (gx[nv] + gx[0])"),
     "lift_phi_for_Phi": ("G += gx[ia(md, k)] * Phi[k];", "G += gx[ia(md, k)] * phi[k];"),
+    "implicit_friction_sign": ("A[k][i] = (k == i ? 1.0 : 0.0) +", "A[k][i] = (k == i ? 1.0 : 0.0) -"),
+    "implicit_newtonian_without_mass_matrix": ("nuh * md->Cm[i * m + k] / md->M[k]", "nuh * md->Cm[i * m + k]"),
 }
 
 PIN_TESTS = ["tests/test_oracle_basis.py", "tests/test_oracle_model.py", "tests/test_oracle_scheme.py",
-             "tests/test_oracle_triangles.py", "tests/test_oracle_lift.py"]
+             "tests/test_oracle_triangles.py", "tests/test_oracle_lift.py", "tests/test_oracle_source.py"]
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
