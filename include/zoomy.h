@@ -111,6 +111,16 @@ zoomy_status zoomy_mesh_permutation(zoomy_ctx *ctx, int64_t *perm_out);
 zoomy_status zoomy_model_set(zoomy_ctx *ctx, int32_t level, const zoomy_friction *friction, double g, double cfl,
                              double h_dry, int32_t dtype);
 
+/* Time treatment of the friction source (Sec. 3.4 closure, Eq. (PDE-source)).  mode 0 (default):
+ * each stage adds the Newtonian bulk stress explicitly and then applies the bottom stress linearly
+ * implicitly (rank-1 Sherman-Morrison).  mode 1: the paper's step_source_implicit: each stage takes
+ * the hyperbolic update only and then applies the whole friction, bulk plus bottom stress, by one
+ * backward-Euler step per cell, (I + dt K) z = y with K_ki = (2k+1) c + (nu/rho)/h^2 C_ik/M_k
+ * (C_ik = int phi_i' phi_k'; h and the bottom coefficient c frozen at the stage result); stable for
+ * stiff thin layers where dt nu/h^2 >> 1.  Structured and triangle contexts; EINVAL for ensembles,
+ * a context with the learned closure, or another mode. */
+zoomy_status zoomy_source_mode(zoomy_ctx *ctx, int32_t mode);
+
 /* Number of variables nv of the current model. */
 zoomy_status zoomy_nvars(zoomy_ctx *ctx, int32_t *nv);
 

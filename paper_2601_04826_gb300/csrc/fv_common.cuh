@@ -49,7 +49,9 @@ struct StageArgs {
     int bc[4];      // x-, x+, y-, y+ (1D: left, right): 0 transmissive, 1 wall
     T g, hdry;
     int fric;       // 0 none, 1 slip + Newtonian, 2 Manning
-    T nu_rho, C_rho, gn2;
+    T nu_rho, C_rho, gn2;        // nu_rho: the explicit Newtonian term (0 when the friction is implicit)
+    int src_implicit;            // 1: friction by backward Euler after the stage (nu_imp = nu / rho)
+    T nu_imp;
     double cfl, dmin, dt_fixed;  // dt_fixed > 0: fixed step; else CFL from ctl->smax[slot_in]
     int slot_in, slot_out;
     DevCtl *ctl;

@@ -79,7 +79,10 @@ __global__ void __launch_bounds__(256) k_stage_1d(StageArgs<T> a)
         y[0] = raw[0] + dt * (a.inv_dx * acc[0]);
 #pragma unroll
         for (int k = 0; k < m; ++k) y[1 + k] = raw[1 + k] + dt * (a.inv_dx * acc[1 + k]) + dt * sa[k];
-        bottom_friction<N, 1, T>(y[0], y + 1, nullptr, a.fric, a.C_rho, a.gn2, dt, a.hdry);
+        if (a.src_implicit)
+            friction_implicit<N, 1, T>(y[0], y + 1, nullptr, a.fric, a.C_rho, a.nu_imp, a.gn2, dt, a.hdry);
+        else
+            bottom_friction<N, 1, T>(y[0], y + 1, nullptr, a.fric, a.C_rho, a.gn2, dt, a.hdry);
         if (STAGE == 2) {
 #pragma unroll
             for (int v = 0; v < nv; ++v) y[v] = T(0.5) * (a.Qn[(int64_t)v * a.ld + i] + y[v]);
@@ -242,7 +245,10 @@ __global__ void __launch_bounds__(128) k_stage_2d(StageArgs<T> a)
                     ya[k] = xprev[ia] + dt * accp[ia] + dt * sa[k];
                     yb[k] = xprev[ib] + dt * accp[ib] + dt * sb[k];
                 }
-                bottom_friction<N, 2, T>(y[0], ya, yb, a.fric, a.C_rho, a.gn2, dt, a.hdry);
+                if (a.src_implicit)
+                    friction_implicit<N, 2, T>(y[0], ya, yb, a.fric, a.C_rho, a.nu_imp, a.gn2, dt, a.hdry);
+                else
+                    bottom_friction<N, 2, T>(y[0], ya, yb, a.fric, a.C_rho, a.gn2, dt, a.hdry);
 #pragma unroll
                 for (int k = 0; k < m; ++k) {
                     y[var_a<N, 2>(k)] = ya[k];

@@ -20,7 +20,7 @@
 
 namespace zoomy {
 
-template <int N, int STAGE>
+template <int N, int STAGE, bool IMP>
 __global__ void __launch_bounds__(32) k_stage_2d_f32(StageArgs<float> a)
 {
     if (*(volatile unsigned int *)&a.ctl->status) return;
@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(32) k_stage_2d_f32(StageArgs<float> a)
     // one warp per CTA: the strip / segment indices and the row loop are uniform across the CTA
     float smax = 0.0f;
     unsigned flag = 0;
-    march_strip<N, STAGE>(a, blockIdx.x % a.nstrips, blockIdx.x / a.nstrips, threadIdx.x, dt, smax, flag);
+    march_strip<N, STAGE, IMP>(a, blockIdx.x % a.nstrips, blockIdx.x / a.nstrips, threadIdx.x, dt, smax, flag);
     if (STAGE == 2) {
         if (flag) atomicOr(&a.ctl->status, flag);
         reduce_smax<float>(a.ctl, a.slot_out, smax);
@@ -46,10 +46,17 @@ static cudaError_t launch_f32(const StageArgs<float> &a, int stage, int wpb, cud
     (void)wpb;  // one warp per CTA
     if (!a.bed) return cudaErrorInvalidValue;
     dim3 grid(a.nstrips * a.nsegs), block(32);
-    if (stage == 1)
-        k_stage_2d_f32<N, 1><<<grid, block, 0, st>>>(a);
-    else
-        k_stage_2d_f32<N, 2><<<grid, block, 0, st>>>(a);
+    if (a.src_implicit) {
+        if (stage == 1)
+            k_stage_2d_f32<N, 1, true><<<grid, block, 0, st>>>(a);
+        else
+            k_stage_2d_f32<N, 2, true><<<grid, block, 0, st>>>(a);
+    } else {
+        if (stage == 1)
+            k_stage_2d_f32<N, 1, false><<<grid, block, 0, st>>>(a);
+        else
+            k_stage_2d_f32<N, 2, false><<<grid, block, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 

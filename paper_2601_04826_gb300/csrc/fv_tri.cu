@@ -295,7 +295,10 @@ __global__ void __launch_bounds__(128) k_stage_tri(TriArgs a)
             ya[k] = raw[var_a<N, 2>(k)] + dt * (acc[var_a<N, 2>(k)] + sa[k]);
             yb[k] = raw[var_b<N>(k)] + dt * (acc[var_b<N>(k)] + sb[k]);
         }
-        bottom_friction<N, 2, float>(y[0], ya, yb, s.fric, s.C_rho, s.gn2, dt, s.hdry);
+        if (s.src_implicit)
+            friction_implicit<N, 2, float>(y[0], ya, yb, s.fric, s.C_rho, s.nu_imp, s.gn2, dt, s.hdry);
+        else
+            bottom_friction<N, 2, float>(y[0], ya, yb, s.fric, s.C_rho, s.gn2, dt, s.hdry);
 #pragma unroll
         for (int k = 0; k < m; ++k) {
             y[var_a<N, 2>(k)] = ya[k];
@@ -373,6 +376,11 @@ zoomy_status tri_run_steps(zoomy_ctx *c, float *Q, int64_t ld, double dt, int ns
     s.hdry = (float)c->hdry;
     s.fric = c->fric.kind;
     s.nu_rho = c->fric.kind == ZOOMY_FRICTION_SLIP_NEWTONIAN ? (float)(c->fric.nu / c->fric.rho) : 0.0f;
+    if (c->src_implicit) {  // friction by backward Euler after the stage: no explicit Newtonian term
+        s.src_implicit = 1;
+        s.nu_imp = s.nu_rho;
+        s.nu_rho = 0.0f;
+    }
     s.C_rho = (float)(c->fric.C / c->fric.rho);
     s.gn2 = (float)(c->g * c->fric.manning_n * c->fric.manning_n);
     s.cfl = c->cfl;

@@ -323,6 +323,74 @@ __device__ __forceinline__ void bottom_friction(T h, T *ya, T *yb, int fric, T C
     }
 }
 
+// Friction fully implicit (the paper's step_source_implicit for the friction ODE of Eq. (PDE-source)):
+// backward Euler (I + dt K) z = y on the moment rows with K_ki = (2k+1) c + (nu/rho)/h^2 C_ik/M_k,
+// the bottom stress (c as in bottom_friction) and the Newtonian bulk stress, h and c frozen at y;
+// then the dry cut.  K = D (c 1 1^T + (nu/rho)/h^2 C), D = diag(2k+1), C positive semi-definite:
+// I + dt K is similar to a symmetric positive-definite matrix, so elimination needs no pivoting.
+template <int N, int D, typename T>
+__device__ __forceinline__ void friction_implicit(T h, T *ya, T *yb, int fric, T C_rho, T nu_rho, T gn2, T dt,
+                                                  T hdry)
+{
+    constexpr int m = N + 1;
+    if (!(h > hdry)) {
+#pragma unroll
+        for (int k = 0; k < m; ++k) {
+            ya[k] = T(0);
+            if constexpr (D == 2) yb[k] = T(0);
+        }
+        return;
+    }
+    if (fric == 0) return;
+    T sa = 0, sb = 0;
+#pragma unroll
+    for (int k = 0; k < m; ++k) {
+        sa += ya[k];
+        if constexpr (D == 2) sb += yb[k];
+    }
+    T c;
+    if (fric == 1) {
+        c = dev_div(C_rho, h);
+    } else {
+        T ub = dev_div(sa, h), vb = dev_div(sb, h);
+        T sp = (D == 2) ? dev_sqrt(ub * ub + vb * vb) : fabs(ub);
+        c = dev_div(gn2 * sp, h * cbrt(h));
+    }
+    const T nuh = fric == 1 ? dev_div(nu_rho, h * h) : T(0);
+    T A[m][m];
+    static_for<0, m>([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        static_for<0, m>([&](auto ii) {
+            constexpr int i = decltype(ii)::value;
+            A[k][i] = (k == i ? T(1) : T(0)) + dt * (T(bedW(k)) * c + nuh * T(visC(i, k)));
+        });
+    });
+#pragma unroll
+    for (int col = 0; col < m; ++col) {
+        const T piv = dev_div(T(1), A[col][col]);
+#pragma unroll
+        for (int r = col + 1; r < m; ++r) {
+            const T f = A[r][col] * piv;
+#pragma unroll
+            for (int j = col + 1; j < m; ++j) A[r][j] -= f * A[col][j];
+            ya[r] -= f * ya[col];
+            if constexpr (D == 2) yb[r] -= f * yb[col];
+        }
+    }
+#pragma unroll
+    for (int k = m - 1; k >= 0; --k) {
+        T za = ya[k], zb = D == 2 ? yb[k] : T(0);
+#pragma unroll
+        for (int j = k + 1; j < m; ++j) {
+            za -= A[k][j] * ya[j];
+            if constexpr (D == 2) zb -= A[k][j] * yb[j];
+        }
+        const T inv = dev_div(T(1), A[k][k]);
+        ya[k] = za * inv;
+        if constexpr (D == 2) yb[k] = zb * inv;
+    }
+}
+
 // Cell wave-speed bound s = |u_mean| + sqrt(g h + sum_{k>=1}|a_k|^2) + sum_{k>=2}|a_k|.
 template <int N, int D, typename T>
 __device__ __forceinline__ T wavespeed(const CellRec<N, D, T> &r, T g)

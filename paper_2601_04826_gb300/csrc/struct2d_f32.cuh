@@ -7,6 +7,7 @@
 
 #include "f32x2.cuh"
 #include "fv_common.cuh"
+#include "model.cuh"
 
 namespace zoomy {
 
@@ -275,8 +276,9 @@ __device__ __forceinline__ void load_row(const StageArgs<float> &a, const RowCtx
     dst[nv] = __ldg(c.bcol + off);
 }
 
-// Process row r with the previous row state P and the current row state C.
-template <int N, int STAGE>
+// Process row r with the previous row state P and the current row state C.  IMP: the friction
+// (bulk + bottom stress) by backward Euler after the stage instead of the default treatment.
+template <int N, int STAGE, bool IMP = false>
 __device__ __forceinline__ void row_body(const StageArgs<float> &a, const RowCtx &c, int r, int r0, int r1, float dt,
                                          float *nxt, RowState<N> &P, RowState<N> &C, float &smax, unsigned &flag)
 {
@@ -381,7 +383,10 @@ __device__ __forceinline__ void row_body(const StageArgs<float> &a, const RowCtx
                 yb[k] = P.acc[var_b<N>(k)];
             }
             const float h = P.acc[0];
-            friction32<N>(h, ya, yb, a.fric, a.C_rho, a.gn2, dt, hdry);
+            if constexpr (IMP)
+                friction_implicit<N, 2, float>(h, ya, yb, a.fric, a.C_rho, a.nu_imp, a.gn2, dt, hdry);
+            else
+                friction32<N>(h, ya, yb, a.fric, a.C_rho, a.gn2, dt, hdry);
             float y[nv];
             y[0] = h;
 #pragma unroll
@@ -433,7 +438,7 @@ __device__ __forceinline__ void zero_state(RowState<N> &S)
 
 // One warp marches its strip (30 columns) over the rows of segment seg: the whole stage for those
 // cells.  smax / flag accumulate the wave speed and status of the cells the lane finishes (stage 2).
-template <int N, int STAGE>
+template <int N, int STAGE, bool IMP = false>
 __device__ __forceinline__ void march_strip(const StageArgs<float> &a, int strip, int seg, int lane, float dt,
                                             float &smax, unsigned &flag)
 {
@@ -458,8 +463,8 @@ __device__ __forceinline__ void march_strip(const StageArgs<float> &a, int strip
     float nxt[nv + 1];
     load_row<N, STAGE>(a, c, r0 - 1, nxt);
     for (int r = r0 - 1; r <= r1; r += 2) {
-        row_body<N, STAGE>(a, c, r, r0, r1, dt, nxt, B, A, smax, flag);
-        if (r + 1 <= r1) row_body<N, STAGE>(a, c, r + 1, r0, r1, dt, nxt, A, B, smax, flag);
+        row_body<N, STAGE, IMP>(a, c, r, r0, r1, dt, nxt, B, A, smax, flag);
+        if (r + 1 <= r1) row_body<N, STAGE, IMP>(a, c, r + 1, r0, r1, dt, nxt, A, B, smax, flag);
     }
 }
 

@@ -231,6 +231,11 @@ static void fill_args(zoomy_ctx *c, StageArgs<T> &a, int64_t ld, double dt)
     a.hdry = T(c->hdry);
     a.fric = c->fric.kind;
     a.nu_rho = c->fric.kind == ZOOMY_FRICTION_SLIP_NEWTONIAN ? T(c->fric.nu / c->fric.rho) : T(0);
+    if (c->src_implicit) {  // friction by backward Euler after the stage: no explicit Newtonian term
+        a.src_implicit = 1;
+        a.nu_imp = a.nu_rho;
+        a.nu_rho = T(0);
+    }
     a.C_rho = T(c->fric.C / c->fric.rho);
     a.gn2 = T(c->g * c->fric.manning_n * c->fric.manning_n);
     a.cfl = c->cfl;
@@ -605,10 +610,21 @@ extern "C" zoomy_status zoomy_closure_set(zoomy_ctx *c, const float *params, con
     if (!c->model_ok || c->kind != ZOOMY_MESH_2D || c->level != 1 || c->dtype != ZOOMY_FP32)
         return set_error(ZOOMY_EINVAL, "zoomy_closure_set: needs a structured 2D level-1 FP32 model");
     if (!(lambda >= 0.0)) return set_error(ZOOMY_EINVAL, "zoomy_closure_set: lambda >= 0");
+    if (c->src_implicit) return set_error(ZOOMY_EINVAL, "zoomy_closure_set: needs the default source mode");
     zoomy_status st = closure_upload(c, params, in_scale, out_scale);
     if (st != ZOOMY_OK) return st;
     c->closure_on = true;
     c->closure_lambda = lambda;
+    return ZOOMY_OK;
+}
+
+extern "C" zoomy_status zoomy_source_mode(zoomy_ctx *c, int32_t mode)
+{
+    if (!c) return set_error(ZOOMY_EINVAL, "zoomy_source_mode: NULL context");
+    if (mode < 0 || mode > 1) return set_error(ZOOMY_EINVAL, "zoomy_source_mode: mode is 0 or 1");
+    if (c->kind == ZOOMY_MESH_ENSEMBLE || c->closure_on)
+        return set_error(ZOOMY_EINVAL, "zoomy_source_mode: not available for ensembles or the learned closure");
+    c->src_implicit = mode;
     return ZOOMY_OK;
 }
 

@@ -31,6 +31,7 @@ struct zoomy_ctx {
     int level = 0, dtype = 0, nv = 0;
     zoomy_friction fric = {0, 0.0, 0.0, 1.0, 0.0};
     double g = 9.81, cfl = 0.45, hdry = 0.0;
+    int src_implicit = 0;  // 0: explicit Newtonian + implicit bottom stress; 1: friction fully implicit
     // device buffers owned by the context
     void *bed_dev = nullptr;
     void *q1 = nullptr;
