@@ -65,6 +65,7 @@ def _declare(L):
     L.or_model_new.restype = vp
     L.or_model_free.argtypes = [vp]
     L.or_model_set_source_mode.argtypes = [vp, C.c_int]
+    L.or_model_set_order.argtypes = [vp, C.c_int]
     L.or_friction_implicit.argtypes = [vp, _dp, C.c_double]
     L.or_model_nv.argtypes = [vp]
     L.or_flux.argtypes = [vp, _dp, C.c_double, C.c_double, _dp]
@@ -133,13 +134,17 @@ class Model:
     """Level-N shallow-moment model in 1D or 2D (variable order documented in the C file)."""
 
     def __init__(self, N, dim, g=9.81, h_dry=1e-6, friction=0, C=0.0, nu=0.0, rho=1.0, manning_n=0.0,
-                 implicit_source=False):
+                 implicit_source=False, order=1):
         self.N, self.dim = N, dim
         self._p = lib().or_model_new(N, dim, g, h_dry, friction, C, nu, rho, manning_n)
         if not self._p:
             raise ValueError("bad model parameters")
         # reading R17: friction (Newtonian + bottom stress) by backward Euler after each stage
         lib().or_model_set_source_mode(self._p, 1 if implicit_source else 0)
+        # reading R18: order 2 = MUSCL reconstruction on 1D and structured 2D meshes
+        if order not in (1, 2):
+            raise ValueError("order is 1 or 2")
+        lib().or_model_set_order(self._p, order)
         self.nv = lib().or_model_nv(self._p)
         self.g, self.h_dry = g, h_dry
 

@@ -167,6 +167,7 @@ typedef struct {
     double Cm[OR_MAXM * OR_MAXM];
     double phi0[OR_MAXM];
     int src_implicit; /* 0: reading R5 (explicit Newtonian, implicit bottom stress); 1: R17 */
+    int order;        /* space order: 1 (reading R6) or 2 (reading R18, structured meshes) */
 } or_model;
 
 /* Variable order.  1D: (h, hA_0..hA_N).  2D: (h, hA_0, hB_0, hA_1..hA_N, hB_1..hB_N),
@@ -197,11 +198,13 @@ or_model *or_model_new(int N, int dim, double g, double h_dry, int fric, double 
     md->nu = nu;
     md->rho = rho;
     md->manning_n = manning_n;
+    md->order = 1;
     or_basis_tables(N, md->M, md->A, md->B, md->Cm, md->phi0);
     return md;
 }
 void or_model_free(or_model *md) { free(md); }
 void or_model_set_source_mode(or_model *md, int mode) { md->src_implicit = mode; }
+void or_model_set_order(or_model *md, int order) { md->order = order; }
 int or_model_nv(const or_model *md) { return md->nv; }
 
 /* Velocity moments alpha_k = hA_k / h, beta_k = hB_k / h; zero where h <= h_dry (R8). */
@@ -660,6 +663,139 @@ void or_friction_implicit(const or_model *md, double *y, double dt)
     }
 }
 
+/* ------------------------------------------------------------------------- */
+/* Second order in space (reading R18): MUSCL on 1D and structured 2D meshes   */
+/* ------------------------------------------------------------------------- */
+
+static double minmod(double a, double b)
+{
+    if (a > 0.0 && b > 0.0) return a < b ? a : b;
+    if (a < 0.0 && b < 0.0) return a > b ? a : b;
+    return 0.0;
+}
+
+/* Reconstruction variables of a state: w = (h, eta = h + b, alpha_0..alpha_N, beta_0..beta_N). */
+static int prim_vars(const or_model *md, const double *q, double b, double *w)
+{
+    double al[OR_MAXM], be[OR_MAXM];
+    velocities(md, q, al, be);
+    w[0] = q[0];
+    w[1] = q[0] + b;
+    for (int k = 0; k < md->m; ++k) {
+        w[2 + k] = al[k];
+        if (md->dim == 2) w[2 + md->m + k] = be[k];
+    }
+    return md->dim == 2 ? 2 + 2 * md->m : 2 + md->m;
+}
+
+/* Neighbour of cell i across its face f (state and bed), the ghost of A9 on boundary faces. */
+static void neighbour(const or_model *md, const or_mesh *me, const double *X, const double *bed, int64_t i,
+                      int f, double *qj, double *bj)
+{
+    double qi[OR_MAXV];
+    int64_t e = i * me->nf + f, j = me->nbr[e];
+    if (j >= 0) {
+        gather(X, me->nc, md->nv, j, qj);
+        *bj = bed ? bed[j] : 0.0;
+    } else {
+        gather(X, me->nc, md->nv, i, qi);
+        ghost(md, qi, me->fbc[e], me->fnx[e], me->fny[e], qj);
+        *bj = bed ? bed[i] : 0.0;
+    }
+}
+
+/* Limited slopes of cell i in direction d (faces 2d and 2d+1 of the cell): sigma = minmod of the
+ * one-sided differences of w, zero for every variable if one of the three cells is dry. */
+static void slopes(const or_model *md, const or_mesh *me, const double *X, const double *bed, int64_t i, int d,
+                   double *sig)
+{
+    double qi[OR_MAXV], ql[OR_MAXV], qr[OR_MAXV], wi[2 + 2 * OR_MAXM], wl[2 + 2 * OR_MAXM], wr[2 + 2 * OR_MAXM];
+    double bl, br;
+    gather(X, me->nc, md->nv, i, qi);
+    neighbour(md, me, X, bed, i, 2 * d, ql, &bl);
+    neighbour(md, me, X, bed, i, 2 * d + 1, qr, &br);
+    int nw = prim_vars(md, qi, bed ? bed[i] : 0.0, wi);
+    prim_vars(md, ql, bl, wl);
+    prim_vars(md, qr, br, wr);
+    int dry = !(qi[0] > md->h_dry) || !(ql[0] > md->h_dry) || !(qr[0] > md->h_dry);
+    for (int v = 0; v < nw; ++v) sig[v] = dry ? 0.0 : minmod(wi[v] - wl[v], wr[v] - wi[v]);
+}
+
+/* Face state of cell i on side s (-1: face 2d, +1: face 2d+1) of direction d:
+ * w + s sigma / 2, the bed b + s (sigma_eta - sigma_h) / 2, as a conserved state. */
+static void face_state(const or_model *md, const double *qi, double bi, const double *sig, int s, double *qf,
+                       double *bf)
+{
+    double w[2 + 2 * OR_MAXM];
+    int nw = prim_vars(md, qi, bi, w);
+    for (int v = 0; v < nw; ++v) w[v] += 0.5 * s * sig[v];
+    *bf = bi + 0.5 * s * (sig[1] - sig[0]);
+    for (int v = 0; v < md->nv; ++v) qf[v] = 0.0;
+    qf[0] = w[0];
+    for (int k = 0; k < md->m; ++k) {
+        qf[ia(md, k)] = w[0] * w[2 + k];
+        if (md->dim == 2) qf[ib(md, k)] = w[0] * w[2 + md->m + k];
+    }
+}
+
+/* Second-order hyperbolic part of cell i: sum over faces of |e| times the face term between the
+ * two reconstructed face states, plus per direction the cell-interior terms
+ *   |e_d| g (h_+ + h_-)/2 (eta_+ - eta_-)                on the normal mean-momentum row,
+ *   |e_d| Btilde_d(Q_- -> Q_+) (Q_+ - Q_-)               (3-point Gauss-Legendre path integral),
+ * which vanish for zero slopes (first order) and for a lake at rest. */
+static void hyperbolic2(const or_model *md, const or_mesh *me, const double *X, const double *bed, int64_t i,
+                        double *acc)
+{
+    int nv = md->nv, ndir = me->nf / 2;
+    double qi[OR_MAXV], term[OR_MAXV];
+    gather(X, me->nc, nv, i, qi);
+    double bi = bed ? bed[i] : 0.0;
+    for (int v = 0; v < nv; ++v) acc[v] = 0.0;
+    for (int d = 0; d < ndir; ++d) {
+        double sig[2 + 2 * OR_MAXM], qm[OR_MAXV], qp[OR_MAXV], bm, bp;
+        slopes(md, me, X, bed, i, d, sig);
+        face_state(md, qi, bi, sig, -1, qm, &bm);
+        face_state(md, qi, bi, sig, +1, qp, &bp);
+        for (int side = 0; side < 2; ++side) {
+            int f = 2 * d + side;
+            int64_t e = i * me->nf + f, j = me->nbr[e];
+            const double *qf = side ? qp : qm;
+            double bf = side ? bp : bm, qn[OR_MAXV], bn;
+            if (j >= 0) {
+                double qjc[OR_MAXV], sj[2 + 2 * OR_MAXM];
+                gather(X, me->nc, nv, j, qjc);
+                slopes(md, me, X, bed, j, d, sj);
+                face_state(md, qjc, bed ? bed[j] : 0.0, sj, side ? -1 : +1, qn, &bn);
+            } else {
+                ghost(md, qf, me->fbc[e], me->fnx[e], me->fny[e], qn);
+                bn = bf;
+            }
+            face_term(md, qf, bf, qn, bn, me->fnx[e], me->fny[e], term);
+            for (int v = 0; v < nv; ++v) acc[v] += me->flen[e] * term[v];
+        }
+        /* cell interior, normal +e_d, face length of direction d */
+        double len = me->flen[i * me->nf + 2 * d], nx = d == 0 ? 1.0 : 0.0, ny = d == 0 ? 0.0 : 1.0;
+        double etap = qp[0] + bp, etam = qm[0] + bm;
+        int row = d == 0 ? ia(md, 0) : ib(md, 0);
+        acc[row] += len * 0.5 * md->g * (qp[0] + qm[0]) * (etap - etam);
+        const double sq[3] = {0.5 - sqrt(15.0) / 10.0, 0.5, 0.5 + sqrt(15.0) / 10.0};
+        const double wq[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+        double Bt[OR_MAXV * OR_MAXV], Bq[OR_MAXV * OR_MAXV], psi[OR_MAXV], dq[OR_MAXV];
+        for (int v = 0; v < nv; ++v) dq[v] = qp[v] - qm[v];
+        for (int v = 0; v < nv * nv; ++v) Bt[v] = 0.0;
+        for (int q = 0; q < 3; ++q) {
+            for (int v = 0; v < nv; ++v) psi[v] = qm[v] + sq[q] * dq[v];
+            or_nc_matrix(md, psi, nx, ny, Bq);
+            for (int v = 0; v < nv * nv; ++v) Bt[v] += wq[q] * Bq[v];
+        }
+        for (int r = 0; r < nv; ++r) {
+            double a = 0.0;
+            for (int c = 0; c < nv; ++c) a += Bt[r * nv + c] * dq[c];
+            acc[r] += len * a;
+        }
+    }
+}
+
 void or_stage(const or_model *md, const or_mesh *me, const double *X, const double *bed, double dt,
               double *Y)
 {
@@ -671,19 +807,23 @@ void or_stage(const or_model *md, const or_mesh *me, const double *X, const doub
         gather(X, nc, nv, i, qi);
         double bi = bed ? bed[i] : 0.0;
         for (int v = 0; v < nv; ++v) acc[v] = 0.0;
-        for (int f = 0; f < me->nf; ++f) {
-            int64_t e = i * me->nf + f;
-            double nx = me->fnx[e], ny = me->fny[e], bj;
-            int64_t j = me->nbr[e];
-            if (j >= 0) {
-                gather(X, nc, nv, j, qj);
-                bj = bed ? bed[j] : 0.0;
-            } else {
-                ghost(md, qi, me->fbc[e], nx, ny, qj);
-                bj = bi;
+        if (md->order == 2 && me->nf != 3) {
+            hyperbolic2(md, me, X, bed, i, acc);
+        } else {
+            for (int f = 0; f < me->nf; ++f) {
+                int64_t e = i * me->nf + f;
+                double nx = me->fnx[e], ny = me->fny[e], bj;
+                int64_t j = me->nbr[e];
+                if (j >= 0) {
+                    gather(X, nc, nv, j, qj);
+                    bj = bed ? bed[j] : 0.0;
+                } else {
+                    ghost(md, qi, me->fbc[e], nx, ny, qj);
+                    bj = bi;
+                }
+                face_term(md, qi, bi, qj, bj, nx, ny, term);
+                for (int v = 0; v < nv; ++v) acc[v] += me->flen[e] * term[v];
             }
-            face_term(md, qi, bi, qj, bj, nx, ny, term);
-            for (int v = 0; v < nv; ++v) acc[v] += me->flen[e] * term[v];
         }
         if (md->src_implicit) {
             for (int v = 0; v < nv; ++v) y[v] = qi[v] - dt / me->area[i] * acc[v];

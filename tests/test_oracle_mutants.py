@@ -39,12 +39,18 @@ MUTANTS = {
     "lift_phi_for_Phi": ("G += gx[ia(md, k)] * Phi[k];", "G += gx[ia(md, k)] * phi[k];"),
     "implicit_friction_sign": ("A[k][i] = (k == i ? 1.0 : 0.0) +", "A[k][i] = (k == i ? 1.0 : 0.0) -"),
     "implicit_newtonian_without_mass_matrix": ("nuh * md->Cm[i * m + k] / md->M[k]", "nuh * md->Cm[i * m + k]"),
+    "order2_interior_pressure_dropped": ("acc[row] += len * 0.5 * md->g * (qp[0] + qm[0]) * (etap - etam);",
+                                         "(void)row;"),
+    "order2_interior_nc_dropped": ("            acc[r] += len * a;", "            (void)a;"),
+    "order2_slopes_unlimited": ("minmod(wi[v] - wl[v], wr[v] - wi[v])", "0.5 * (wr[v] - wl[v])"),
+    "order2_face_bed_not_reconstructed": ("*bf = bi + 0.5 * s * (sig[1] - sig[0]);", "*bf = bi;"),
 }
 
 FIRST_PIN = {"tri_": "tests/test_oracle_triangles.py", "lift_": "tests/test_oracle_lift.py",
-             "implicit_": "tests/test_oracle_source.py"}
+             "implicit_": "tests/test_oracle_source.py", "order2_": "tests/test_oracle_order2.py"}
 PIN_TESTS = ["tests/test_oracle_basis.py", "tests/test_oracle_model.py", "tests/test_oracle_scheme.py",
-             "tests/test_oracle_triangles.py", "tests/test_oracle_lift.py", "tests/test_oracle_source.py"]
+             "tests/test_oracle_triangles.py", "tests/test_oracle_lift.py", "tests/test_oracle_source.py",
+             "tests/test_oracle_order2.py"]
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
