@@ -183,8 +183,12 @@ def run_ours(args, rank, world, local_rank):
     ctx = zoomy.Context(zoomy.mesh_2d(N_SIDE, N_SIDE, bathymetry=b), LEVEL, fr, cfl=CFL, dtype=zoomy.FP32)
     Q = torch.tensor(Q0, dtype=torch.float32, device=dev)
 
+    if args.order == 2:
+        zoomy.zoomy_space_order(ctx.ctx, 2)
     # launch configuration from the autotuner (or given, for profiling runs), then warm-up
-    if args.rows_per_warp:
+    if args.order == 2:
+        tuned_rows = None  # the second-order kernel is cell-centric
+    elif args.rows_per_warp:
         zoomy.zoomy_tune_set(ctx.ctx, args.rows_per_warp, 1)
         tuned_rows = args.rows_per_warp
     else:
@@ -232,7 +236,8 @@ def run_ours(args, rank, world, local_rank):
     dom = 2 if avg2 >= avg1 else 1
     avg = avg2 if dom == 2 else avg1
     achieved = BYTES_STAGE[dom] * nc / (avg * 1e-3) / 1e9
-    traffic = ncu_traffic() if dom == 2 else None
+    traffic = ncu_traffic() if dom == 2 and args.order == 1 else None
+    kname = f"k_stage_2d_f32<2,{dom}>" if args.order == 1 else f"k_stage_order2<2,2,float,{dom}>"
     value = job_throughput(nc, args.steps, ms * 1e-3, world)
     step_bytes = (BYTES_STAGE[1] + BYTES_STAGE[2]) * nc
     line = {
@@ -254,8 +259,9 @@ def run_ours(args, rank, world, local_rank):
                    "l2": "inputs larger than L2 (Q 117 MB + stage buffer 117 MB + bed 17 MB per replica)",
                    "step_hbm_fraction": step_bytes / (ms / args.steps * 1e-3) / 1e9 / hbm,
                    "rows_per_warp": tuned_rows,
+                   "space_order": args.order,
                    "sim_time_advanced": t_sim},
-        "roofline": {"bound": "hbm", "kernel": f"k_stage_2d_f32<2,{dom}>", "achieved": achieved, "peak": hbm,
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
                      "algorithmic_bytes_per_launch": BYTES_STAGE[dom] * nc,
                      "avg_launch_ms": {"stage1": avg1, "stage2": avg2}},
@@ -640,6 +646,8 @@ def main():
                          "ensemble: 512 ragged level-1 members in one persistent launch; closure: learned "
                          "closure vs level 4, time to T = 2 on 1024^2")
     ap.add_argument("--closure-members", type=int, default=256, help="level-4 training runs (closure workload)")
+    ap.add_argument("--order", type=int, choices=[1, 2], default=1,
+                    help="space order of the grid workload (1: the benchmark scheme; 2: MUSCL)")
     ap.add_argument("--tri-side", type=int, default=1415,
                     help="lattice side of the triangle workload (1415: ~4M triangles; smaller for profiling runs)")
     ap.add_argument("--closure-train-side", type=int, default=128, help="grid side of the training runs")

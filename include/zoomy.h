@@ -121,6 +121,19 @@ zoomy_status zoomy_model_set(zoomy_ctx *ctx, int32_t level, const zoomy_friction
  * a context with the learned closure, or another mode. */
 zoomy_status zoomy_source_mode(zoomy_ctx *ctx, int32_t mode);
 
+/* Order in space.  1 (default): the first-order scheme above.  2: MUSCL reconstruction (the
+ * second-order building block the paper names with its gradient reconstruction, Sec. 2.1.2): per
+ * direction, minmod-limited slopes of (h, eta = h + b, velocity moments), zero next to dry cells;
+ * face states w +- slope/2 with the bed b +- (slope_eta - slope_h)/2; the first-order face term
+ * (hydrostatic reconstruction, path-conservative Rusanov flux, pressure difference, path integral
+ * of the nonconservative product) between reconstructed face states; per cell and direction the
+ * interior terms g (h_+ + h_-)/2 (eta_+ - eta_-) on the normal mean momentum and
+ * Btilde(Q_- -> Q_+)(Q_+ - Q_-).  Well-balanced (lake at rest), second order on smooth solutions,
+ * no new extrema at shocks; the CFL step is still taken from the cell wave speeds (a CFL number of
+ * at most 0.3 is advisable).  1D and structured 2D contexts, FP32 or FP64; EINVAL for triangles,
+ * ensembles, a context with the learned closure, or another order. */
+zoomy_status zoomy_space_order(zoomy_ctx *ctx, int32_t order);
+
 /* Number of variables nv of the current model. */
 zoomy_status zoomy_nvars(zoomy_ctx *ctx, int32_t *nv);
 

@@ -126,7 +126,8 @@ __device__ __forceinline__ void make_cell(CellRec<N, D, T> &r, T h, T b, const T
     r.s1 = s1;
     static_for<0, m>([&](auto kk) {
         constexpr int k = decltype(kk)::value;
-        T saa = 0, sab = 0, sbb = 0;
+        T saa = 0;
+        [[maybe_unused]] T sab = 0, sbb = 0;  // 2D only
         static_for<0, m>([&](auto ii) {
             constexpr int i = decltype(ii)::value;
             static_for<0, m>([&](auto jj) {
@@ -236,10 +237,12 @@ __device__ __forceinline__ void face_term(const CellRec<N, D, T> &L, const Frame
         }
         static_for<1, m>([&](auto kk) {
             constexpr int k = decltype(kk)::value;
-            T rn = 0, rt = 0;
+            T rn = 0;
+            [[maybe_unused]] T rt = 0;  // 2D only
             static_for<1, m>([&](auto ll) {
                 constexpr int l = decltype(ll)::value;
-                T en = 0, et = 0;
+                T en = 0;
+                [[maybe_unused]] T et = 0;  // 2D only
                 static_for<0, m>([&](auto jj) {
                     constexpr int j = decltype(jj)::value;
                     constexpr double w = ncB(k, j, l);
@@ -266,7 +269,8 @@ __device__ __forceinline__ void newtonian(const CellRec<N, D, T> &r, T nu_rho, T
     const T f = r.h > T(0) ? dev_div(nu_rho, r.h) : T(0);
     static_for<0, m>([&](auto kk) {
         constexpr int k = decltype(kk)::value;
-        T xa = 0, xb = 0;
+        T xa = 0;
+        [[maybe_unused]] T xb = 0;  // 2D only
         static_for<0, m>([&](auto ii) {
             constexpr int i = decltype(ii)::value;
             constexpr double w = visC(i, k);

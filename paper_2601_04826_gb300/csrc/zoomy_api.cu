@@ -250,6 +250,7 @@ static void fill_args(zoomy_ctx *c, StageArgs<T> &a, int64_t ld, double dt)
 template <typename T>
 static cudaError_t launch_stage(zoomy_ctx *c, const StageArgs<T> &a, int stage)
 {
+    if (c->order == 2) return launch_stage_order2<T>(c->dim, c->level, a, stage, c->nsm, c->stream);
     if constexpr (sizeof(T) == 4) {
         // the specialised FP32 kernel indexes with 32-bit offsets
         if (c->dim == 2 && (int64_t)c->nv * a.ld < (1LL << 31))
@@ -610,7 +611,8 @@ extern "C" zoomy_status zoomy_closure_set(zoomy_ctx *c, const float *params, con
     if (!c->model_ok || c->kind != ZOOMY_MESH_2D || c->level != 1 || c->dtype != ZOOMY_FP32)
         return set_error(ZOOMY_EINVAL, "zoomy_closure_set: needs a structured 2D level-1 FP32 model");
     if (!(lambda >= 0.0)) return set_error(ZOOMY_EINVAL, "zoomy_closure_set: lambda >= 0");
-    if (c->src_implicit) return set_error(ZOOMY_EINVAL, "zoomy_closure_set: needs the default source mode");
+    if (c->src_implicit || c->order != 1)
+        return set_error(ZOOMY_EINVAL, "zoomy_closure_set: needs the default source mode and first order");
     zoomy_status st = closure_upload(c, params, in_scale, out_scale);
     if (st != ZOOMY_OK) return st;
     c->closure_on = true;
@@ -625,6 +627,17 @@ extern "C" zoomy_status zoomy_source_mode(zoomy_ctx *c, int32_t mode)
     if (c->kind == ZOOMY_MESH_ENSEMBLE || c->closure_on)
         return set_error(ZOOMY_EINVAL, "zoomy_source_mode: not available for ensembles or the learned closure");
     c->src_implicit = mode;
+    return ZOOMY_OK;
+}
+
+extern "C" zoomy_status zoomy_space_order(zoomy_ctx *c, int32_t order)
+{
+    if (!c) return set_error(ZOOMY_EINVAL, "zoomy_space_order: NULL context");
+    if (order < 1 || order > 2) return set_error(ZOOMY_EINVAL, "zoomy_space_order: order is 1 or 2");
+    if (order == 2 && (c->kind == ZOOMY_MESH_TRI || c->kind == ZOOMY_MESH_ENSEMBLE || c->closure_on))
+        return set_error(ZOOMY_EINVAL, "zoomy_space_order: order 2 needs a 1D or structured 2D context "
+                                       "without the learned closure");
+    c->order = order;
     return ZOOMY_OK;
 }
 

@@ -32,6 +32,7 @@ struct zoomy_ctx {
     zoomy_friction fric = {0, 0.0, 0.0, 1.0, 0.0};
     double g = 9.81, cfl = 0.45, hdry = 0.0;
     int src_implicit = 0;  // 0: explicit Newtonian + implicit bottom stress; 1: friction fully implicit
+    int order = 1;         // space order: 1, or 2 (MUSCL, fv_order2.cu; 1D and structured 2D)
     // device buffers owned by the context
     void *bed_dev = nullptr;
     void *q1 = nullptr;

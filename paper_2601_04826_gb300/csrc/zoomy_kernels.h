@@ -13,6 +13,9 @@ template <typename T>
 cudaError_t launch_stage_struct(int dim, int level, const StageArgs<T> &a, int stage, int warps_per_block,
                                 cudaStream_t st);
 
+// second order in space (fv_order2.cu): 1D and structured 2D grids, FP32 / FP64
+template <typename T>
+cudaError_t launch_stage_order2(int dim, int level, const StageArgs<T> &a, int stage, int nsm, cudaStream_t st);
 cudaError_t launch_stage_2d_f32(int level, const StageArgs<float> &a, int stage, int warps_per_block,
                                 cudaStream_t st);
 

@@ -68,6 +68,7 @@ _SIGNATURES = [
     ("zoomy_closure_eval", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]),
     ("zoomy_closure_engine", C.c_int, [C.c_void_p, C.c_int32]),
     ("zoomy_source_mode", C.c_int, [C.c_void_p, C.c_int32]),
+    ("zoomy_space_order", C.c_int, [C.c_void_p, C.c_int32]),
     ("zoomy_lift3d", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_int64]),
     ("zoomy_mlp_create", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
     ("zoomy_mlp_destroy", C.c_int, [C.c_void_p]),
@@ -247,6 +248,10 @@ def zoomy_closure_engine(ctx, engine):
 
 def zoomy_source_mode(ctx, mode):
     _check(lib().zoomy_source_mode(ctx, mode))
+
+
+def zoomy_space_order(ctx, order):
+    _check(lib().zoomy_space_order(ctx, order))
 
 
 def zoomy_lift3d(ctx, Q, ld, zeta, out, ldo):
