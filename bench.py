@@ -563,6 +563,44 @@ def run_lift(args):
             "gpu_launches": args.steps, "clocks": clk.summary()}
 
 
+def run_vam(args):
+    """The VAM predictor-corrector in 1D: a small solitary-like hump on depth 1 (2000 cells on [0, 20],
+    walls, FP64), time per step (wave-speed reduction, predictor, banded pressure assembly, banded
+    solve, corrector).  Prints its own JSON line."""
+    import numpy as np
+    import torch
+
+    from paper_2601_04826_gb300 import build, zoomy
+
+    build.build()
+    n, L = 2000, 20.0
+    x = (np.arange(n) + 0.5) * L / n
+    Q0 = np.zeros((5, n))
+    Q0[0] = 1.0 + 0.2 / np.cosh(np.sqrt(0.75 * 0.2) * (x - 5.0)) ** 2
+    Q0[1] = Q0[0] * np.sqrt(9.81 * 1.2) * (1.0 - 1.0 / Q0[0])
+    ctx = zoomy.Context(zoomy.mesh_1d(n, 0.0, L, bc=(1, 1)), 1, zoomy.friction(0), cfl=0.45, dtype=zoomy.FP64)
+    ctx.vam(True)
+    Q = torch.tensor(Q0, dtype=torch.float64, device="cuda")
+    ctx.step(Q, nsteps=args.warmup, dt=0.0)
+    Q.copy_(torch.tensor(Q0, dtype=torch.float64))
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ctx.step(Q, nsteps=args.steps, dt=0.0, sync=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = zoomy.zoomy_sync(ctx.ctx)
+    ms = e0.elapsed_time(e1)
+    ctx.close()
+    return {"metric": "time per VAM predictor-corrector step", "value": 1e3 * ms / args.steps, "unit": "us/step",
+            "cell_updates_per_s": n * args.steps / (ms * 1e-3), "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "1D non-hydrostatic VAM, 2000 cells on [0,20], depth 1 with a 0.2 hump, walls, "
+                                   "adaptive CFL 0.45", "sim_time_advanced": t},
+            "gpu_launches": 5 * args.steps}
+
+
 def oracle_window_run(side, nsteps):
     """The oracle on a side x side window of the workload (cells of the 2048^2 grid, walls)."""
     import numpy as np
@@ -640,7 +678,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     ap.add_argument("--workload", choices=["grid", "tri", "ensemble", "closure", "closure-kernels", "dambreak1d",
-                                           "lift"],
+                                           "lift", "vam"],
                     default="grid",
                     help="grid: the 2048^2 level-2 benchmark (default); tri: the ~4M-triangle level-3 dam break; "
                          "ensemble: 512 ragged level-1 members in one persistent launch; closure: learned "
@@ -679,6 +717,8 @@ def main():
         line = run_dambreak1d(args) if rank == 0 else None
     elif args.workload == "lift":
         line = run_lift(args) if rank == 0 else None
+    elif args.workload == "vam":
+        line = run_vam(args) if rank == 0 else None
     else:
         line = run_ours(args, rank, world, local_rank)
     if rank == 0 and line is not None:

@@ -198,6 +198,7 @@ extern "C" zoomy_status zoomy_lift3d(zoomy_ctx *c, const void *Q, int64_t ld, in
 {
     zoomy_status st = check_step_args(c, Q, ld, 0.0, 0, "zoomy_lift3d");
     if (st != ZOOMY_OK) return st;
+    if (c->vam) return set_error(ZOOMY_EINVAL, "zoomy_lift3d: not defined for the VAM model");
     if (c->kind == ZOOMY_MESH_ENSEMBLE) return set_error(ZOOMY_EINVAL, "zoomy_lift3d: not for ensemble contexts");
     if (!out || !zeta) return set_error(ZOOMY_EINVAL, "zoomy_lift3d: NULL output or levels");
     if (K < 1 || K > LIFT_MAXK) return set_error(ZOOMY_EINVAL, "zoomy_lift3d: K in [1, %d]", LIFT_MAXK);

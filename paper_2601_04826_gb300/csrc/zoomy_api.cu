@@ -116,6 +116,8 @@ extern "C" zoomy_status zoomy_mesh_destroy(zoomy_ctx *c)
     cudaFree(c->qdev_host);
     cudaFree(c->closure_d);
     cudaFree(c->closure_pred);
+    cudaFree(c->vam_band);
+    cudaFree(c->vam_rhs);
     cudaFree(c->closure_tc);
     for (cudaEvent_t ev : c->prof_events) cudaEventDestroy(ev);
     tri_free(c);
@@ -171,6 +173,7 @@ extern "C" zoomy_status zoomy_model_set(zoomy_ctx *c, int32_t level, const zoomy
     c->cfl = cfl;
     c->hdry = h_dry;
     c->nv = c->dim == 1 ? level + 2 : 2 * level + 3;
+    c->vam = 0;  // a new model leaves the VAM mode
     if (c->dtype != dtype || !c->bed_dev) {
         cudaFree(c->bed_dev);
         c->bed_dev = nullptr;
@@ -264,6 +267,8 @@ static zoomy_status run_steps(zoomy_ctx *c, T *Q, int64_t ld, double dt, int nst
 {
     if constexpr (sizeof(T) == 4) {
         if (c->closure_on) return closure_run_steps(c, Q, ld, dt, nsteps);
+    } else {
+        if (c->vam) return vam_run_steps(c, Q, ld, dt, nsteps);
     }
     T *Q1 = (T *)c->q1;
     if (dt <= 0.0) {
@@ -372,6 +377,7 @@ extern "C" zoomy_status zoomy_max_wavespeed(zoomy_ctx *c, const void *Q, int64_t
 {
     zoomy_status st = check_step_args(c, Q, ld, 0.0, 0, "zoomy_max_wavespeed");
     if (st != ZOOMY_OK) return st;
+    if (c->vam) return set_error(ZOOMY_EINVAL, "zoomy_max_wavespeed: not defined for the VAM model");
     if (!out) return set_error(ZOOMY_EINVAL, "zoomy_max_wavespeed: NULL output");
     ZCHECK(cudaMemsetAsync(c->ctl_aux, 0, sizeof(DevCtl), c->stream));
     cudaError_t e = c->dtype == ZOOMY_FP64

@@ -33,6 +33,8 @@ struct zoomy_ctx {
     double g = 9.81, cfl = 0.45, hdry = 0.0;
     int src_implicit = 0;  // 0: explicit Newtonian + implicit bottom stress; 1: friction fully implicit
     int order = 1;         // space order: 1, or 2 (MUSCL, fv_order2.cu; 1D and structured 2D)
+    int vam = 0;           // 1: the non-hydrostatic VAM predictor-corrector (vam.cu), 1D FP64
+    double *vam_band = nullptr, *vam_rhs = nullptr;  // its banded pressure system
     // device buffers owned by the context
     void *bed_dev = nullptr;
     void *q1 = nullptr;
@@ -91,6 +93,8 @@ void tri_free(zoomy_ctx *c);
 void ens_free(zoomy_ctx *c);
 // learned closure (fv_closure.cu)
 zoomy_status closure_run_steps(zoomy_ctx *c, float *Q, int64_t ld, double dt, int nsteps);
+// VAM predictor-corrector (vam.cu)
+zoomy_status vam_run_steps(zoomy_ctx *c, double *Q, int64_t ld, double dt, int nsteps);
 zoomy_status closure_upload(zoomy_ctx *c, const float *params, const float *in_scale, const float *out_scale);
 zoomy_status tri_run_steps(zoomy_ctx *c, float *Q, int64_t ld, double dt, int nsteps);
 }  // namespace zoomy

@@ -69,6 +69,7 @@ _SIGNATURES = [
     ("zoomy_closure_engine", C.c_int, [C.c_void_p, C.c_int32]),
     ("zoomy_source_mode", C.c_int, [C.c_void_p, C.c_int32]),
     ("zoomy_space_order", C.c_int, [C.c_void_p, C.c_int32]),
+    ("zoomy_vam_set", C.c_int, [C.c_void_p, C.c_int32]),
     ("zoomy_lift3d", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_int64]),
     ("zoomy_mlp_create", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
     ("zoomy_mlp_destroy", C.c_int, [C.c_void_p]),
@@ -252,6 +253,10 @@ def zoomy_source_mode(ctx, mode):
 
 def zoomy_space_order(ctx, order):
     _check(lib().zoomy_space_order(ctx, order))
+
+
+def zoomy_vam_set(ctx, enable=1):
+    _check(lib().zoomy_vam_set(ctx, enable))
 
 
 def zoomy_lift3d(ctx, Q, ld, zeta, out, ldo):
@@ -453,6 +458,11 @@ class Context:
 
     def mass(self, Q):
         return zoomy_mass(self.ctx, Q, self._ld(Q))
+
+    def vam(self, enable=True):
+        """Switch a 1D FP64 context to the VAM model (or back); the state then has zoomy_nvars rows."""
+        zoomy_vam_set(self.ctx, 1 if enable else 0)
+        self.nv = zoomy_nvars(self.ctx)
 
     def tune(self, rows_per_warp, warps_per_block):
         zoomy_tune_set(self.ctx, rows_per_warp, warps_per_block)

@@ -1,0 +1,109 @@
+"""The VAM predictor-corrector on the GPU (zoomy_vam_set) against the oracle: smooth states with walls
+and with transmissive ends, the standing-wave dispersion against linear wave theory, lake at rest;
+mode checks."""
+import numpy as np
+import pytest
+
+from gpu_util import rel_l1, to_device
+from oracle import vam
+
+pytestmark = pytest.mark.gpu
+G = 9.81
+
+
+@pytest.fixture(scope="module")
+def Z():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_04826_gb300 import build, zoomy
+
+    build.build()
+    return zoomy
+
+
+def vam_ctx(Z, n, L, bc):
+    ctx = Z.Context(Z.mesh_1d(n, 0.0, L, bc=bc), 1, Z.friction(0), g=G, cfl=0.45, dtype=1)
+    ctx.vam(True)
+    assert ctx.nv == 5
+    return ctx
+
+
+def smooth_state(n, L, seed):
+    rng = np.random.default_rng(seed)
+    x = (np.arange(n) + 0.5) * L / n
+    Q = np.zeros((5, n))
+    Q[0] = 1.0 + 0.15 * np.exp(-((x - 0.45 * L) ** 2) / (0.01 * L * L))
+    Q[1] = Q[0] * 0.1 * np.sin(2 * np.pi * x / L)
+    Q[2] = Q[0] * 0.03 * np.cos(3 * np.pi * x / L)
+    Q[3] = Q[0] * 0.02 * rng.normal(size=n)
+    Q[4] = Q[0] * 0.02 * rng.normal(size=n)
+    return Q
+
+
+@pytest.mark.parametrize("bc", [(1, 1), (0, 0), (1, 0)])
+def test_matches_oracle(Z, bc):
+    n, L, nsteps = 157, 2.0, 25
+    Q0 = smooth_state(n, L, seed=sum(bc))
+    ctx = vam_ctx(Z, n, L, bc)
+    Q = to_device(Q0, 1)
+    tg = ctx.step(Q, nsteps=nsteps, dt=0.0)
+    got = Q.cpu().numpy()
+    ctx.close()
+    ref, tr, _ = vam.step(Q0, nsteps, L / n, g=G, bc=bc, cfl=0.45)
+    assert tg == pytest.approx(tr, rel=1e-12)
+    err = rel_l1(got, ref)
+    assert np.all(err <= 1e-10), err
+
+
+def test_standing_wave_dispersion(Z):
+    H, kH, n = 1.0, 1.0, 200
+    k = kH / H
+    L = np.pi / k
+    x = (np.arange(n) + 0.5) * L / n
+    Q0 = np.zeros((5, n))
+    Q0[0] = H + 1e-3 * np.cos(k * x)
+    ctx = vam_ctx(Z, n, L, (1, 1))
+    Q = to_device(Q0, 1)
+    hs, ts, t = [Q0[0, 0]], [0.0], 0.0
+    for _ in range(2000):
+        t += ctx.step(Q, nsteps=1, dt=0.0)
+        hs.append(float(Q[0, 0]))
+        ts.append(t)
+        if hs[-1] < H:
+            break
+    ctx.close()
+    y0, y1 = hs[-2] - H, hs[-1] - H
+    tz = ts[-2] + (ts[-1] - ts[-2]) * y0 / (y0 - y1)
+    c2 = (np.pi / (2 * tz) / k) ** 2 / (G * H)
+    assert abs(c2 - np.tanh(kH) / kH) < 6e-3 * np.tanh(kH) / kH, c2
+
+
+def test_lake_at_rest_bitwise(Z):
+    Q0 = np.zeros((5, 64))
+    Q0[0] = 0.7
+    ctx = vam_ctx(Z, 64, 1.0, (1, 1))
+    Q = to_device(Q0, 1)
+    ctx.step(Q, nsteps=30, dt=0.0)
+    got = Q.cpu().numpy()
+    ctx.close()
+    np.testing.assert_array_equal(got, Q0)
+
+
+def test_mode_checks(Z):
+    ctx = Z.Context(Z.mesh_2d(8, 8), 1, Z.friction(0), dtype=1)
+    with pytest.raises(Z.ZoomyError):
+        Z.zoomy_vam_set(ctx.ctx, 1)
+    ctx.close()
+    ctx = Z.Context(Z.mesh_1d(16, 0.0, 1.0), 1, Z.friction(0), dtype=0)
+    with pytest.raises(Z.ZoomyError):  # FP64 only
+        Z.zoomy_vam_set(ctx.ctx, 1)
+    ctx.close()
+    ctx = vam_ctx(Z, 16, 1.0, (1, 1))
+    Q = to_device(np.ones((5, 16)), 1)
+    with pytest.raises(Z.ZoomyError):
+        ctx.max_wavespeed(Q)
+    ctx.vam(False)
+    assert ctx.nv == 3
+    ctx.close()
