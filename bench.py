@@ -563,10 +563,19 @@ def run_lift(args):
             "gpu_launches": args.steps, "clocks": clk.summary()}
 
 
+def vam_launches_per_step(n):
+    """Wave speed, predictor, assembly, correction, and 1 + ceil(log2 N) reduction levels (N = ceil(n / 2))."""
+    N, levels, s = (n + 1) // 2, 0, 1
+    while s < N:
+        levels += 1
+        s *= 2
+    return 5 + levels
+
+
 def run_vam(args):
     """The VAM predictor-corrector in 1D: a small solitary-like hump on depth 1 (2000 cells on [0, 20],
-    walls, FP64), time per step (wave-speed reduction, predictor, banded pressure assembly, banded
-    solve, corrector).  Prints its own JSON line."""
+    walls, FP64), time per step (wave-speed reduction, predictor, block-tridiagonal pressure assembly,
+    cyclic-reduction levels, corrector).  Prints its own JSON line."""
     import numpy as np
     import torch
 
@@ -598,7 +607,7 @@ def run_vam(args):
             "warmup": args.warmup, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "1D non-hydrostatic VAM, 2000 cells on [0,20], depth 1 with a 0.2 hump, walls, "
                                    "adaptive CFL 0.45", "sim_time_advanced": t},
-            "gpu_launches": 5 * args.steps}
+            "gpu_launches": vam_launches_per_step(n) * args.steps}
 
 
 def oracle_window_run(side, nsteps):

@@ -143,7 +143,8 @@ zoomy_status zoomy_space_order(zoomy_ctx *ctx, int32_t order);
  * or fixed); corrector: the non-hydrostatic pressure (p0, p1) per cell that makes
  * Q** = Q* - dt S(p), S = (0, d(h p0)/dx, d(h p1)/dx - (3 p0 - p1) dh/dx, -2 p1, 6 (p0 - p1)),
  * satisfy h du0/dx + d(h u1)/dx/3 + u1 dh/dx/3 + 2 w0 = 0 and h du0/dx + u1 dh/dx - 2 w1 = 0 (central
- * differences, mirrored ghosts; a banded linear system solved on the GPU); Q^{n+1} = Q**.  The
+ * differences, mirrored ghosts; a block-tridiagonal linear system, two cells per block, solved on the
+ * GPU by cyclic reduction); Q^{n+1} = Q**.  The
  * depth must stay positive (ZOOMY_ENEGDEPTH otherwise).  enable = 0 returns to the level-N model.
  * EINVAL for other contexts, the learned closure, order 2 or the implicit friction mode;
  * zoomy_max_wavespeed and zoomy_lift3d are not defined in this mode (EINVAL). */

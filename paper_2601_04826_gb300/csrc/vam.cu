@@ -12,11 +12,21 @@
 //     satisfies R0 = h du0/dx + d(h u1)/dx/3 + u1 dh/dx/3 + 2 w0 = 0 and R1 = h du0/dx + u1 dh/dx - 2 w1 = 0
 //     with central differences and mirrored ghosts (u0, u1 and their momenta change sign at walls).
 //
-// The constraints are linear in p with a stencil of two cells on each side, so the matrix is banded
-// (unknowns interleaved (p0_i, p1_i): 5 sub- and 5 super-diagonals).  It is assembled without any
-// symbolic derivation: probing with the 10 vectors that are 1 on one component of every fifth cell
-// (cells five apart never share a row) gives every band entry as R(probe) - R(0).  The banded system
-// is solved by Gaussian elimination with partial pivoting in one warp (1D problems are small).
+// The constraints are linear in p with a stencil of two cells on each side.  Grouping two cells per
+// block (unknowns (p0, p1) of cells 2I and 2I+1) makes the system block tridiagonal with 4 x 4 blocks
+//   A_I x_{I-1} + D_I x_I + C_I x_{I+1} = f_I,  I = 0 .. N-1,  N = ceil(nc / 2)
+// (an odd line gets one dummy cell with p = 0).  The entries come without any symbolic derivation:
+// probing with the 10 vectors that are 1 on one component of every fifth cell (cells five apart never
+// share a row) gives every entry as R(probe) - R(0), one thread per cell and probe.  The system is
+// solved by parallel cyclic reduction: with Y_J = D_J^{-1} (A_J | C_J | f_J), level s replaces
+//   D_I <- D_I - A_I YC_{I-s} - C_I YA_{I+s},  A_I <- -A_I YA_{I-s},  C_I <- -C_I YC_{I+s},
+//   f_I <- f_I - A_I Yf_{I-s} - C_I Yf_{I+s}
+// (row I then couples to I -+ 2s); after ceil(log2 N) levels no coupling is left and x_I = Yf_I.
+// Every level is one launch with a half-warp per block row (lane = entry (r, c)): the update, then
+// Gauss-Jordan elimination with partial pivoting inside the 4 x 4 block for the new Y_I.  No pivoting
+// across blocks: the constraint operator is close to symmetric positive definite once each cell's two
+// rows are combined (3 R0 + R1, R0), so elimination in any order is stable, and the probed 4 x 4 blocks
+// keep their own pivoting.
 #include <cmath>
 #include <cstdint>
 
@@ -28,13 +38,16 @@
 
 namespace zoomy {
 
-constexpr int VKL = 5, VKU = 5, VW = 2 * VKL + VKU + 1;  // band half-widths, stored row width (with fill)
+constexpr int RS = 64;  // block row: A [16] at 0, C [16] at 16, D [16] at 32, f [4] at 48 (entry r * 4 + c)
+constexpr int YS = 48;  // Y_J: YA [16] at 0, YC [16] at 16, Yf [4] at 32
+constexpr int PCR_ROWS = 8;  // block rows per 128-thread CTA of the reduction
 
 struct VamArgs {
     double *Q;        // state [5][ld] (in: Q^n, out: Q^{n+1})
     double *Qs;       // predictor result Q* [5][ld]
-    double *band;     // [2 nc][VW]: A(r, c) at band[r * VW + (c - r + VKL)]
-    double *rhs;      // [2 nc]: -R(0), then the solution p
+    double *rows;     // [N][RS] block rows of the pressure system (updated in place by the reduction)
+    double *Y[2];     // [N][YS] ping-pong Y of the reduction levels
+    double *rhs;      // [4 N]: the solution p, unknown 2 j + comp for cell j
     int64_t ld, nc;
     double dx, g, cfl;
     int bcl, bcr;     // 1 wall, 0 transmissive
@@ -194,160 +207,154 @@ __device__ __forceinline__ void vresidual(const VamArgs &a, const Probe &pr, int
     R[1] = h * du0 + u1 * dh - 2.0 * w1;
 }
 
-// Band entries by probing, and the right-hand side -R(0); the fill columns start at zero.
+// Block rows by probing: thread (i, q) of cell i evaluates R(0) (q = 0, which also writes f = -R(0)
+// and the zero entries outside the stencil) or R(probe q) - R(0) for the q-th (color, component).
 __global__ void __launch_bounds__(128) k_vam_assemble(VamArgs a)
 {
     if (*(volatile unsigned int *)&a.ctl->status) return;
     const double dt = *(volatile double *)&a.ctl->dt_last;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.nc; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < 11 * a.nc; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / 11, I = i >> 1;
+        const int q = (int)(t - 11 * i);
+        double *blk = a.rows + I * RS;
+        const int r0w = 2 * (int)(i & 1);  // this cell's two rows within the block
         double r0[2];
         vresidual(a, Probe{-1, 0, nullptr}, i, dt, r0);
-        for (int r = 0; r < 2; ++r) {
-            double *row = a.band + (2 * i + r) * VW;
-            for (int w = 0; w < VW; ++w) row[w] = 0.0;
-            a.rhs[2 * i + r] = -r0[r];
-        }
-        for (int color = 0; color < 5; ++color)
-            for (int comp = 0; comp < 2; ++comp) {
-                // the one cell of this color within the stencil i-2..i+2 of row i
-                const int64_t j = i - 2 + (((color - (int)((i - 2 + 10 * 5) % 5)) % 5 + 5) % 5);
-                if (j < 0 || j >= a.nc) continue;
-                double rp[2];
-                vresidual(a, Probe{color, comp, nullptr}, i, dt, rp);
-                for (int r = 0; r < 2; ++r) {
-                    const int64_t row = 2 * i + r, col = 2 * j + comp;
-                    a.band[row * VW + (col - row + VKL)] = rp[r] - r0[r];
+        // column within the 12 of the block row (A | D | C) for unknown (cell j, comp)
+        auto put = [&](int64_t j, int comp, int r, double v) {
+            const int col = 2 * (int)(j - 2 * (I - 1)) + comp;
+            blk[16 * (col < 4 ? 0 : col < 8 ? 2 : 1) + 4 * (r0w + r) + (col & 3)] = v;
+        };
+        if (q == 0) {
+            for (int r = 0; r < 2; ++r) blk[48 + r0w + r] = -r0[r];
+            const int64_t jout = (i & 1) ? 2 * I - 2 : 2 * I + 3;  // the one cell of the block row outside the stencil
+            for (int r = 0; r < 2; ++r)
+                for (int comp = 0; comp < 2; ++comp) put(jout, comp, r, 0.0);
+            if (i == a.nc - 1 && !(i & 1)) {
+                // odd line: the dummy cell 2I+1 has rows p = 0
+                for (int e = 0; e < 8; ++e) {
+                    blk[8 + e] = 0.0;
+                    blk[16 + 8 + e] = 0.0;
+                    blk[32 + 8 + e] = 0.0;
                 }
+                blk[32 + 10] = 1.0;
+                blk[32 + 15] = 1.0;
+                blk[48 + 2] = 0.0;
+                blk[48 + 3] = 0.0;
             }
+            continue;
+        }
+        const int color = (q - 1) >> 1, comp = (q - 1) & 1;
+        // the one cell of this color within the stencil i-2..i+2 of row i
+        const int64_t j = i - 2 + (((color - (int)((i - 2 + 10 * 5) % 5)) % 5 + 5) % 5);
+        if (j < 0 || j >= a.nc) {
+            for (int r = 0; r < 2; ++r) put(j, comp, r, 0.0);
+            continue;
+        }
+        double rp[2];
+        vresidual(a, Probe{color, comp, nullptr}, i, dt, rp);
+        for (int r = 0; r < 2; ++r) put(j, comp, r, rp[r] - r0[r]);
     }
 }
 
-// Gaussian elimination with partial pivoting on the band by one warp; the solution overwrites rhs.
-// The elimination is a chain over the columns, so its working set stays in shared memory: the six
-// rows k..k+5 that column k touches (row r in slot r % 6, column c at index c % 16; every row covers
-// 16 consecutive columns from r - 5, entries left of the current column are kept at zero), the next
-// row prefetched into registers during each step, the finished row k written back for the back
-// substitution, which keeps the last solution values in a ring of 16.
-__global__ void __launch_bounds__(32) k_vam_solve(VamArgs a)
+// One level of the block cyclic reduction (s = 0: only Y_I = D_I^{-1} (A_I | C_I | f_I)); `last`
+// writes the solution.  A half-warp per block row; lane l holds entry (r, c) = (l / 4, l % 4).
+__global__ void __launch_bounds__(128) k_vam_pcr(VamArgs a, int64_t N, int64_t s, const double *__restrict__ Yin,
+                                                 double *__restrict__ Yout, int last)
 {
     if (*(volatile unsigned int *)&a.ctl->status) return;
-    constexpr unsigned F = 0xffffffffu;
-    __shared__ double win[6][16];
-    __shared__ double rw[6];
-    __shared__ double xs[16];
-    const int lane = threadIdx.x;
-    const int64_t n = 2 * a.nc;
-    double *band = a.band, *rhs = a.rhs;
-    // row r of the band (offsets 0..15 = columns r-5..r+10) into its window slot
-    auto load = [&](int64_t r, double &val, double &rv) {
-        val = 0.0;
-        rv = 0.0;
-        if (r < n) {
-            if (lane < 16) val = band[r * VW + lane];
-            if (lane == 16) rv = rhs[r];
-        }
-    };
-    auto put = [&](int64_t r, double val, double rv) {
-        if (r < n) {
-            if (lane < 16) win[r % 6][(r - 5 + lane) & 15] = val;
-            if (lane == 16) rw[r % 6] = rv;
-        }
-    };
-    for (int64_t r = 0; r < 6; ++r) {
-        double val, rv;
-        load(r, val, rv);
-        put(r, val, rv);
-    }
-    __syncwarp();
-    for (int64_t k = 0; k < n; ++k) {
-        double nval, nrv;
-        load(k + 6, nval, nrv);  // in flight during this step
-        const int64_t rmax = k + VKL < n ? k + VKL : n - 1;
-        const int64_t cmax = k + VKL + VKU < n ? k + VKL + VKU : n - 1;
-        const int kc = (int)(k & 15);
-        // pivot: the largest |A(r, k)|, r = k..rmax (lowest row on ties)
-        double v = -1.0;
-        int best = lane;
-        if (lane <= rmax - k) v = fabs(win[(k + lane) % 6][kc]);
+    __shared__ double S[PCR_ROWS][4][16];
+    const int hw = threadIdx.x >> 4, l = threadIdx.x & 15, r = l >> 2, c = l & 3;
+    const int64_t I = (int64_t)blockIdx.x * PCR_ROWS + hw;
+    if (I >= N) return;  // the whole half-warp
+    const unsigned mask = 0xffffu << (threadIdx.x & 16);
+    double *row = a.rows + I * RS;
+    double D, A, C, F;
+    if (s > 0) {
+        double arow[4], crow[4];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const double ov = __shfl_xor_sync(F, v, o);
-            const int ob = __shfl_xor_sync(F, best, o);
-            if (ov > v || (ov == v && ob < best)) {
-                v = ov;
-                best = ob;
-            }
+        for (int k = 0; k < 4; ++k) {
+            arow[k] = row[4 * r + k];
+            crow[k] = row[16 + 4 * r + k];
         }
-        if (!(v > 0.0)) {
-            if (lane == 0) atomicOr(&a.ctl->status, DEV_NAN);  // singular pressure system
-            return;
-        }
-        const int sk = (int)(k % 6), sb = (int)((k + best) % 6);
-        if (best != 0) {
-            if (lane < 16) {
-                const double t = win[sk][lane];
-                win[sk][lane] = win[sb][lane];
-                win[sb][lane] = t;
-            }
-            if (lane == 16) {
-                const double t = rw[sk];
-                rw[sk] = rw[sb];
-                rw[sb] = t;
-            }
-        }
-        __syncwarp();
-        const double inv = 1.0 / win[sk][kc];
-        const int nr = (int)(rmax - k), ncol = (int)(cmax - k);
-        // multipliers of the rows below (read before any of them changes)
-        double l = 0.0;
-        if (lane < nr) l = win[(k + 1 + lane) % 6][kc] * inv;
-        __syncwarp();
-        for (int idx = lane; idx < nr * ncol; idx += 32) {
-            const int rr = idx / ncol, cc = 1 + idx % ncol;
-            const double lr = win[(k + 1 + rr) % 6][kc] * inv;  // column k is not written in this loop
-            win[(k + 1 + rr) % 6][(k + cc) & 15] -= lr * win[sk][(k + cc) & 15];
-        }
-        __syncwarp();
-        if (lane < nr) {
-            rw[(k + 1 + lane) % 6] -= l * rw[sk];
-            win[(k + 1 + lane) % 6][kc] = 0.0;  // eliminated
-        }
-        // the finished row k (columns k..cmax) and its right-hand side go back for the substitution
-        if (lane <= ncol) band[k * VW + VKL + lane] = win[sk][(k + lane) & 15];
-        if (lane == 16) rhs[k] = rw[sk];
-        __syncwarp();
-        put(k + 6, nval, nrv);  // slot of row k is free now
-        __syncwarp();
-    }
-    // back substitution; the next row of U and its right-hand side are loaded during each step
-    auto loadu = [&](int64_t r, double &bv, double &rv) {
-        bv = 0.0;
-        rv = 0.0;
-        if (r >= 0) {
-            if (lane <= VKL + VKU) bv = band[r * VW + VKL + lane];
-            if (lane == 16) rv = rhs[r];
-        }
-    };
-    double bv, rv;
-    loadu(n - 1, bv, rv);
-    for (int64_t k = n - 1; k >= 0; --k) {
-        double nbv, nrv;
-        loadu(k - 1, nbv, nrv);
-        const int64_t cmax = k + VKL + VKU < n ? k + VKL + VKU : n - 1;
-        const int ncol = (int)(cmax - k);
-        double s = 0.0;
-        if (lane >= 1 && lane <= ncol) s = bv * xs[(k + lane) & 15];
+        D = row[32 + l];
+        F = row[48 + r];
+        A = 0.0;
+        C = 0.0;
+        if (I - s >= 0) {
+            const double *Ym = Yin + (I - s) * YS;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(F, s, o);
-        const double rk = __shfl_sync(F, rv, 16);
-        if (lane == 0) {
-            const double x = (rk - s) / bv;  // lane 0 holds the diagonal
-            xs[k & 15] = x;
-            rhs[k] = x;
+            for (int k = 0; k < 4; ++k) {
+                D -= arow[k] * Ym[16 + 4 * k + c];
+                A -= arow[k] * Ym[4 * k + c];
+                F -= arow[k] * Ym[32 + k];
+            }
         }
-        __syncwarp();
-        bv = nbv;
-        rv = nrv;
+        if (I + s < N) {
+            const double *Yp = Yin + (I + s) * YS;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                D -= crow[k] * Yp[4 * k + c];
+                C -= crow[k] * Yp[16 + 4 * k + c];
+                F -= crow[k] * Yp[32 + k];
+            }
+        }
+        __syncwarp(mask);  // every lane has read the old row
+        row[l] = A;
+        row[16 + l] = C;
+        row[32 + l] = D;
+        if (c == 0) row[48 + r] = F;
+    } else {
+        A = row[l];
+        C = row[16 + l];
+        D = row[32 + l];
+        F = row[48 + r];
+    }
+    // Gauss-Jordan elimination with partial pivoting on [D | A | C | f]
+    double(*M)[16] = S[hw];
+    bool singular = false;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        M[r][c] = D;
+        M[r][4 + c] = A;
+        M[r][8 + c] = C;
+        if (c == 0) M[r][12] = F;
+        __syncwarp(mask);
+        int piv = k;
+        double best = fabs(M[k][k]);
+#pragma unroll
+        for (int q = k + 1; q < 4; ++q) {
+            const double v = fabs(M[q][k]);
+            if (v > best) {
+                best = v;
+                piv = q;
+            }
+        }
+        singular |= !(best > 0.0);
+        const int rs = r == k ? piv : (r == piv ? k : r);  // the row that lands in row r after the swap
+        const double ip = 1.0 / M[piv][k];
+        const double p0 = M[piv][c] * ip, p1 = M[piv][4 + c] * ip, p2 = M[piv][8 + c] * ip, pf = M[piv][12] * ip;
+        if (r == k) {
+            D = p0;
+            A = p1;
+            C = p2;
+            F = pf;
+        } else {
+            const double m = M[rs][k];
+            D = M[rs][c] - m * p0;
+            A = M[rs][4 + c] - m * p1;
+            C = M[rs][8 + c] - m * p2;
+            F = M[rs][12] - m * pf;
+        }
+        __syncwarp(mask);
+    }
+    if (singular && l == 0) atomicOr(&a.ctl->status, DEV_NAN);  // singular pressure block
+    double *y = Yout + I * YS;
+    y[l] = A;
+    y[16 + l] = C;
+    if (c == 0) {
+        y[32 + r] = F;
+        if (last && 4 * I + r < 2 * a.nc) a.rhs[4 * I + r] = F;
     }
 }
 
@@ -371,9 +378,12 @@ __global__ void __launch_bounds__(128) k_vam_correct(VamArgs a)
 zoomy_status vam_run_steps(zoomy_ctx *c, double *Q, int64_t ld, double dt, int nsteps)
 {
     VamArgs a;
+    const int64_t N = (c->nc + 1) / 2;
     a.Q = Q;
     a.Qs = (double *)c->q1;
-    a.band = c->vam_band;
+    a.rows = c->vam_band;
+    a.Y[0] = c->vam_band + N * RS;
+    a.Y[1] = a.Y[0] + N * YS;
     a.rhs = c->vam_rhs;
     a.ld = ld;
     a.nc = c->nc;
@@ -384,18 +394,29 @@ zoomy_status vam_run_steps(zoomy_ctx *c, double *Q, int64_t ld, double dt, int n
     a.bcr = c->bc[1];
     a.ctl = c->ctl;
     a.dt_fixed = dt;
-    int64_t blocks = (c->nc + 127) / 128;
-    if (blocks > (int64_t)c->nsm * 4) blocks = (int64_t)c->nsm * 4;
-    const unsigned grid = (unsigned)blocks;
+    // FP64 work per cell: one-warp CTAs spread short lines over more SMs
+    const int threads = c->nc < 65536 ? 32 : 128;
+    auto grid_for = [&](int64_t work) {
+        int64_t b = (work + threads - 1) / threads;
+        const int64_t cap = (int64_t)c->nsm * (threads == 32 ? 16 : 4);
+        return (unsigned)(b < cap ? b : cap);
+    };
+    const unsigned grid = grid_for(c->nc), grid_asm = grid_for(11 * c->nc);
+    const unsigned grid_pcr = (unsigned)((N + PCR_ROWS - 1) / PCR_ROWS);
     for (int k = 0; k < nsteps; ++k) {
         a.slot_in = k & 1;
         a.slot_out = k & 1;  // the wave-speed reduction of step k fills the slot its predictor reads
-        k_vam_wavespeed<<<grid, 128, 0, c->stream>>>(a);
+        k_vam_wavespeed<<<grid, threads, 0, c->stream>>>(a);
         a.slot_out = (k + 1) & 1;  // the predictor clears the next step's slot
-        k_vam_predict<<<grid, 128, 0, c->stream>>>(a);
-        k_vam_assemble<<<grid, 128, 0, c->stream>>>(a);
-        k_vam_solve<<<1, 32, 0, c->stream>>>(a);
-        k_vam_correct<<<grid, 128, 0, c->stream>>>(a);
+        k_vam_predict<<<grid, threads, 0, c->stream>>>(a);
+        k_vam_assemble<<<grid_asm, threads, 0, c->stream>>>(a);
+        int cur = 0;
+        k_vam_pcr<<<grid_pcr, 16 * PCR_ROWS, 0, c->stream>>>(a, N, 0, a.Y[1], a.Y[0], N == 1);
+        for (int64_t s = 1; s < N; s *= 2) {
+            k_vam_pcr<<<grid_pcr, 16 * PCR_ROWS, 0, c->stream>>>(a, N, s, a.Y[cur], a.Y[cur ^ 1], 2 * s >= N);
+            cur ^= 1;
+        }
+        k_vam_correct<<<grid, threads, 0, c->stream>>>(a);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "VAM step launch");
     }
@@ -416,8 +437,9 @@ extern "C" zoomy_status zoomy_vam_set(zoomy_ctx *c, int32_t enable)
         if (c->closure_on || c->order != 1 || c->src_implicit)
             return set_error(ZOOMY_EINVAL, "zoomy_vam_set: not with the closure, order 2 or implicit friction");
         if (!c->vam_band) {
-            cudaError_t e = cudaMalloc(&c->vam_band, sizeof(double) * (size_t)(2 * c->nc) * VW);
-            if (e == cudaSuccess) e = cudaMalloc(&c->vam_rhs, sizeof(double) * (size_t)(2 * c->nc));
+            const size_t N = (size_t)(c->nc + 1) / 2;
+            cudaError_t e = cudaMalloc(&c->vam_band, sizeof(double) * N * (RS + 2 * YS));
+            if (e == cudaSuccess) e = cudaMalloc(&c->vam_rhs, sizeof(double) * 4 * N);
             if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
         }
         c->vam = 1;

@@ -57,6 +57,40 @@ def test_matches_oracle(Z, bc):
     assert np.all(err <= 1e-10), err
 
 
+@pytest.mark.parametrize("n,bc", [(1, (1, 1)), (2, (0, 1)), (3, (1, 0)), (16, (1, 1)), (33, (0, 0))])
+def test_line_lengths(Z, n, bc):
+    """Short and odd lines (one block row, a dummy cell, few reduction levels)."""
+    L, nsteps = 0.1 * n, 6
+    Q0 = smooth_state(n, L, seed=n)
+    ctx = vam_ctx(Z, n, L, bc)
+    Q = to_device(Q0, 1)
+    ctx.step(Q, nsteps=nsteps, dt=0.0)
+    got = Q.cpu().numpy()
+    ctx.close()
+    ref, _, _ = vam.step(Q0, nsteps, L / n, g=G, bc=bc, cfl=0.45)
+    # per variable, against its own magnitude (a lone cell between walls keeps momenta at round-off)
+    scale = np.maximum(np.abs(ref).max(axis=1), 1e-3)
+    err = np.abs(got - ref).max(axis=1) / scale
+    assert np.all(err <= 1e-10), err
+
+
+def test_bench_size(Z):
+    """The timed workload's size and launch configuration (2000 cells, 11 reduction levels)."""
+    n, L, nsteps = 2000, 20.0, 2
+    x = (np.arange(n) + 0.5) * L / n
+    Q0 = np.zeros((5, n))
+    Q0[0] = 1.0 + 0.2 / np.cosh(np.sqrt(0.75 * 0.2) * (x - 5.0)) ** 2
+    Q0[1] = Q0[0] * np.sqrt(G * 1.2) * (1.0 - 1.0 / Q0[0])
+    ctx = vam_ctx(Z, n, L, (1, 1))
+    Q = to_device(Q0, 1)
+    tg = ctx.step(Q, nsteps=nsteps, dt=0.0)
+    got = Q.cpu().numpy()
+    ctx.close()
+    ref, tr, _ = vam.step(Q0, nsteps, L / n, g=G, bc=(1, 1), cfl=0.45)
+    assert tg == pytest.approx(tr, rel=1e-12)
+    assert np.all(rel_l1(got, ref) <= 1e-10), rel_l1(got, ref)
+
+
 def test_standing_wave_dispersion(Z):
     H, kH, n = 1.0, 1.0, 200
     k = kH / H
