@@ -64,15 +64,16 @@ __device__ __forceinline__ double vq(const VamArgs &a, const double *Q, int v, i
     return Q[v * a.ld + j];
 }
 
-__device__ __forceinline__ double vspeed(const double *q, double g)
+__device__ __forceinline__ double vspeed(const double *q, double rh, double g)
 {
-    const double u0 = q[1] / q[0], u1 = q[2] / q[0];
+    const double u0 = q[1] * rh, u1 = q[2] * rh;
     return fabs(u0) + sqrt(g * q[0] + u1 * u1) + fabs(u1);
 }
 
-__device__ __forceinline__ void vflux(const double *q, double *F)
+// F(q); rh = 1 / h (one division per state, the velocities as products)
+__device__ __forceinline__ void vflux(const double *q, double rh, double *F)
 {
-    const double h = q[0], u0 = q[1] / h, u1 = q[2] / h, w0 = q[3] / h, w1 = q[4] / h, w2 = -(w0 + w1);
+    const double h = q[0], u0 = q[1] * rh, u1 = q[2] * rh, w0 = q[3] * rh, w1 = q[4] * rh, w2 = -(w0 + w1);
     F[0] = h * u0;
     F[1] = h * u0 * u0 + h * u1 * u1 / 3.0;
     F[2] = 2.0 * h * u0 * u1;
@@ -84,25 +85,35 @@ __device__ __forceinline__ void vflux(const double *q, double *F)
 __device__ __forceinline__ void vface(const double *qL, const double *qR, double g, double *dm, double *dp)
 {
     double FL[5], FR[5], dq[5], bt[5] = {0, 0, 0, 0, 0};
-    vflux(qL, FL);
-    vflux(qR, FR);
+    const double rhL = 1.0 / qL[0], rhR = 1.0 / qR[0];
+    vflux(qL, rhL, FL);
+    vflux(qR, rhR, FR);
     for (int v = 0; v < 5; ++v) dq[v] = qR[v] - qL[v];
     const double sq[3] = {0.5 - 0.38729833462074168852, 0.5, 0.5 + 0.38729833462074168852};
     const double wq[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
     for (int k = 0; k < 3; ++k) {
         double p[5];
         for (int v = 0; v < 5; ++v) p[v] = qL[v] + sq[k] * dq[v];
-        const double h = p[0], u0 = p[1] / h, w0 = p[3] / h, w1 = p[4] / h, w2 = -(w0 + w1);
+        const double h = p[0], rh = 1.0 / h, u0 = p[1] * rh, w0 = p[3] * rh, w1 = p[4] * rh, w2 = -(w0 + w1);
         bt[1] += wq[k] * g * h * dq[0];
         bt[2] += wq[k] * (-u0) * dq[2];
         bt[4] += wq[k] * (w2 / 5.0 - w0) * dq[2];
     }
-    const double sL = vspeed(qL, g), sR = vspeed(qR, g), sf = sL > sR ? sL : sR;
+    const double sL = vspeed(qL, rhL, g), sR = vspeed(qR, rhR, g), sf = sL > sR ? sL : sR;
     for (int v = 0; v < 5; ++v) {
         const double c = 0.5 * (FR[v] - FL[v]) + 0.5 * bt[v];
         dm[v] = c - 0.5 * sf * dq[v];
         dp[v] = c + 0.5 * sf * dq[v];
     }
+}
+
+// Programmatic dependent launch: every VAM kernel waits for its predecessor on the stream to complete
+// (with its memory visible), then lets the next kernel launch, so each launch and CTA ramp overlaps
+// the kernel before it.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 __device__ __forceinline__ double vam_dt(const VamArgs &a)
@@ -115,12 +126,13 @@ __device__ __forceinline__ double vam_dt(const VamArgs &a)
 // max s over Q^n into the slot of this step
 __global__ void __launch_bounds__(128) k_vam_wavespeed(VamArgs a)
 {
+    pdl_enter();
     double s = 0.0;
     unsigned flag = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.nc; i += (int64_t)gridDim.x * blockDim.x) {
         double q[5];
         for (int v = 0; v < 5; ++v) q[v] = a.Q[v * a.ld + i];
-        const double si = vspeed(q, a.g);
+        const double si = vspeed(q, 1.0 / q[0], a.g);
         if (!(q[0] > 0.0)) flag |= q[0] < 0.0 ? DEV_NEGDEPTH : DEV_NAN;
         s = (si > s || si != si) ? si : s;
     }
@@ -130,6 +142,7 @@ __global__ void __launch_bounds__(128) k_vam_wavespeed(VamArgs a)
 
 __global__ void __launch_bounds__(128) k_vam_predict(VamArgs a)
 {
+    pdl_enter();
     if (*(volatile unsigned int *)&a.ctl->status) return;
     const double dt = vam_dt(a);
     if (!(dt > 0.0)) {
@@ -141,16 +154,26 @@ __global__ void __launch_bounds__(128) k_vam_predict(VamArgs a)
         a.ctl->dt_last = dt;
         a.ctl->smax_d[a.slot_out] = 0ull;  // the next step's slot
     }
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.nc; i += (int64_t)gridDim.x * blockDim.x) {
-        double ql[5], qc[5], qr[5], dm[5], dp[5], dml[5], dpl[5];
-        for (int v = 0; v < 5; ++v) {
-            ql[v] = vq(a, a.Q, v, i - 1);
-            qc[v] = vq(a, a.Q, v, i);
-            qr[v] = vq(a, a.Q, v, i + 1);
+    // a warp per 31 cells: lane j evaluates the face between cells i-1 and i (i = 31 w + j) once;
+    // cell i (j < 31) takes that face's D+ and, from lane j+1, the D- of its right face
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * blockDim.x / 32;
+    for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w * 31 < a.nc; w += nw) {
+        const int64_t i = 31 * w + lane;
+        double ql[5], qr[5], dm[5], dp[5];
+        if (i <= a.nc) {
+            for (int v = 0; v < 5; ++v) {
+                ql[v] = vq(a, a.Q, v, i - 1);
+                qr[v] = vq(a, a.Q, v, i);
+            }
+            vface(ql, qr, a.g, dm, dp);
+        } else {
+            for (int v = 0; v < 5; ++v) qr[v] = dm[v] = dp[v] = 0.0;
         }
-        vface(ql, qc, a.g, dml, dpl);  // face i-1/2: this cell is on the right
-        vface(qc, qr, a.g, dm, dp);    // face i+1/2: this cell is on the left
-        for (int v = 0; v < 5; ++v) a.Qs[v * a.ld + i] = qc[v] - dt / a.dx * (dpl[v] + dm[v]);
+        for (int v = 0; v < 5; ++v) {
+            const double dmr = __shfl_down_sync(0xffffffffu, dm[v], 1);
+            if (lane < 31 && i < a.nc) a.Qs[v * a.ld + i] = qr[v] - dt / a.dx * (dp[v] + dmr);
+        }
     }
 }
 
@@ -199,7 +222,7 @@ __device__ __forceinline__ void vresidual(const VamArgs &a, const Probe &pr, int
         if (a.bcr == 1) qr[1] = -qr[1], qr[2] = -qr[2];
     }
     const double i2dx = 0.5 / a.dx;
-    const double h = qc[0], u1 = qc[2] / h, w0 = qc[3] / h, w1 = qc[4] / h;
+    const double h = qc[0], rh = 1.0 / h, u1 = qc[2] * rh, w0 = qc[3] * rh, w1 = qc[4] * rh;
     const double dh = (qr[0] - ql[0]) * i2dx;
     const double du0 = (qr[1] / qr[0] - ql[1] / ql[0]) * i2dx;
     const double dhu1 = (qr[2] - ql[2]) * i2dx;
@@ -211,6 +234,7 @@ __device__ __forceinline__ void vresidual(const VamArgs &a, const Probe &pr, int
 // and the zero entries outside the stencil) or R(probe q) - R(0) for the q-th (color, component).
 __global__ void __launch_bounds__(128) k_vam_assemble(VamArgs a)
 {
+    pdl_enter();
     if (*(volatile unsigned int *)&a.ctl->status) return;
     const double dt = *(volatile double *)&a.ctl->dt_last;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < 11 * a.nc; t += (int64_t)gridDim.x * blockDim.x) {
@@ -262,6 +286,7 @@ __global__ void __launch_bounds__(128) k_vam_assemble(VamArgs a)
 __global__ void __launch_bounds__(128) k_vam_pcr(VamArgs a, int64_t N, int64_t s, const double *__restrict__ Yin,
                                                  double *__restrict__ Yout, int last)
 {
+    pdl_enter();
     if (*(volatile unsigned int *)&a.ctl->status) return;
     __shared__ double S[PCR_ROWS][4][16];
     const int hw = threadIdx.x >> 4, l = threadIdx.x & 15, r = l >> 2, c = l & 3;
@@ -310,7 +335,9 @@ __global__ void __launch_bounds__(128) k_vam_pcr(VamArgs a, int64_t N, int64_t s
         D = row[32 + l];
         F = row[48 + r];
     }
-    // Gauss-Jordan elimination with partial pivoting on [D | A | C | f]
+    // Gauss-Jordan elimination with partial pivoting on [D | A | C | f], fraction-free: every row but
+    // the pivot row becomes pk * row - m * pivot row, and each row is divided by its diagonal at the
+    // end (one division per lane instead of one per step); magnitudes compare as bit patterns
     double(*M)[16] = S[hw];
     bool singular = false;
 #pragma unroll
@@ -320,35 +347,40 @@ __global__ void __launch_bounds__(128) k_vam_pcr(VamArgs a, int64_t N, int64_t s
         M[r][8 + c] = C;
         if (c == 0) M[r][12] = F;
         __syncwarp(mask);
+        constexpr unsigned long long MAG = 0x7fffffffffffffffull;
         int piv = k;
-        double best = fabs(M[k][k]);
+        unsigned long long best = (unsigned long long)__double_as_longlong(M[k][k]) & MAG;
 #pragma unroll
         for (int q = k + 1; q < 4; ++q) {
-            const double v = fabs(M[q][k]);
+            const unsigned long long v = (unsigned long long)__double_as_longlong(M[q][k]) & MAG;
             if (v > best) {
                 best = v;
                 piv = q;
             }
         }
-        singular |= !(best > 0.0);
+        singular |= best == 0ull || best >= 0x7ff0000000000000ull;  // zero, infinite or NaN pivot
         const int rs = r == k ? piv : (r == piv ? k : r);  // the row that lands in row r after the swap
-        const double ip = 1.0 / M[piv][k];
-        const double p0 = M[piv][c] * ip, p1 = M[piv][4 + c] * ip, p2 = M[piv][8 + c] * ip, pf = M[piv][12] * ip;
+        const double pk = M[piv][k];
+        const double P0 = M[piv][c], P1 = M[piv][4 + c], P2 = M[piv][8 + c], Pf = M[piv][12];
         if (r == k) {
-            D = p0;
-            A = p1;
-            C = p2;
-            F = pf;
+            D = P0;
+            A = P1;
+            C = P2;
+            F = Pf;
         } else {
             const double m = M[rs][k];
-            D = M[rs][c] - m * p0;
-            A = M[rs][4 + c] - m * p1;
-            C = M[rs][8 + c] - m * p2;
-            F = M[rs][12] - m * pf;
+            D = pk * M[rs][c] - m * P0;
+            A = pk * M[rs][4 + c] - m * P1;
+            C = pk * M[rs][8 + c] - m * P2;
+            F = pk * M[rs][12] - m * Pf;
         }
         __syncwarp(mask);
     }
     if (singular && l == 0) atomicOr(&a.ctl->status, DEV_NAN);  // singular pressure block
+    const double ip = 1.0 / __shfl_sync(mask, D, 5 * r, 16);  // row r's diagonal, lane (r, r)
+    A *= ip;
+    C *= ip;
+    F *= ip;
     double *y = Yout + I * YS;
     y[l] = A;
     y[16 + l] = C;
@@ -360,6 +392,7 @@ __global__ void __launch_bounds__(128) k_vam_pcr(VamArgs a, int64_t N, int64_t s
 
 __global__ void __launch_bounds__(128) k_vam_correct(VamArgs a)
 {
+    pdl_enter();
     if (*(volatile unsigned int *)&a.ctl->status) return;
     const double dt = *(volatile double *)&a.ctl->dt_last;
     unsigned flag = 0;
@@ -373,6 +406,22 @@ __global__ void __launch_bounds__(128) k_vam_correct(VamArgs a)
         if (q[0] <= 0.0) flag |= DEV_NEGDEPTH;
     }
     if (flag) atomicOr(&a.ctl->status, flag);
+}
+
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*k)(KArgs...), unsigned grid, unsigned block, cudaStream_t st, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
 }
 
 zoomy_status vam_run_steps(zoomy_ctx *c, double *Q, int64_t ld, double dt, int nsteps)
@@ -402,22 +451,24 @@ zoomy_status vam_run_steps(zoomy_ctx *c, double *Q, int64_t ld, double dt, int n
         return (unsigned)(b < cap ? b : cap);
     };
     const unsigned grid = grid_for(c->nc), grid_asm = grid_for(11 * c->nc);
+    const unsigned grid_pred = grid_for((c->nc + 30) / 31 * 32);  // a warp per 31 cells
     const unsigned grid_pcr = (unsigned)((N + PCR_ROWS - 1) / PCR_ROWS);
+    const cudaStream_t st = c->stream;
     for (int k = 0; k < nsteps; ++k) {
         a.slot_in = k & 1;
         a.slot_out = k & 1;  // the wave-speed reduction of step k fills the slot its predictor reads
-        k_vam_wavespeed<<<grid, threads, 0, c->stream>>>(a);
+        cudaError_t e = launch_pdl(k_vam_wavespeed, grid, threads, st, a);
         a.slot_out = (k + 1) & 1;  // the predictor clears the next step's slot
-        k_vam_predict<<<grid, threads, 0, c->stream>>>(a);
-        k_vam_assemble<<<grid_asm, threads, 0, c->stream>>>(a);
+        if (e == cudaSuccess) e = launch_pdl(k_vam_predict, grid_pred, threads, st, a);
+        if (e == cudaSuccess) e = launch_pdl(k_vam_assemble, grid_asm, threads, st, a);
         int cur = 0;
-        k_vam_pcr<<<grid_pcr, 16 * PCR_ROWS, 0, c->stream>>>(a, N, 0, a.Y[1], a.Y[0], N == 1);
-        for (int64_t s = 1; s < N; s *= 2) {
-            k_vam_pcr<<<grid_pcr, 16 * PCR_ROWS, 0, c->stream>>>(a, N, s, a.Y[cur], a.Y[cur ^ 1], 2 * s >= N);
+        const unsigned bp = 16 * PCR_ROWS;
+        if (e == cudaSuccess) e = launch_pdl(k_vam_pcr, grid_pcr, bp, st, a, N, (int64_t)0, (const double *)a.Y[1], a.Y[0], (int)(N == 1));
+        for (int64_t s = 1; s < N && e == cudaSuccess; s *= 2) {
+            e = launch_pdl(k_vam_pcr, grid_pcr, bp, st, a, N, s, (const double *)a.Y[cur], a.Y[cur ^ 1], (int)(2 * s >= N));
             cur ^= 1;
         }
-        k_vam_correct<<<grid, threads, 0, c->stream>>>(a);
-        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = launch_pdl(k_vam_correct, grid, threads, st, a);
         if (e != cudaSuccess) return cuda_fail(e, "VAM step launch");
     }
     return ZOOMY_OK;
