@@ -125,6 +125,20 @@ def test_lake_at_rest_bitwise(Z):
     np.testing.assert_array_equal(got, Q0)
 
 
+def test_fixed_dt(Z):
+    """dt > 0: the predictor and the corrector take the given step, not the CFL one."""
+    n, L, nsteps, dt = 96, 1.5, 12, 2e-4
+    Q0 = smooth_state(n, L, seed=7)
+    ctx = vam_ctx(Z, n, L, (1, 0))
+    Q = to_device(Q0, 1)
+    tg = ctx.step(Q, nsteps=nsteps, dt=dt)
+    got = Q.cpu().numpy()
+    ctx.close()
+    ref, tr, _ = vam.step(Q0, nsteps, L / n, g=G, bc=(1, 0), dt=dt)
+    assert tg == pytest.approx(nsteps * dt, rel=1e-12) and tr == pytest.approx(nsteps * dt, rel=1e-12)
+    assert np.all(rel_l1(got, ref) <= 1e-10), rel_l1(got, ref)
+
+
 def test_mode_checks(Z):
     ctx = Z.Context(Z.mesh_2d(8, 8), 1, Z.friction(0), dtype=1)
     with pytest.raises(Z.ZoomyError):
@@ -140,4 +154,9 @@ def test_mode_checks(Z):
         ctx.max_wavespeed(Q)
     ctx.vam(False)
     assert ctx.nv == 3
+    with pytest.raises(Z.ZoomyError):  # enable is 0 or 1
+        Z.zoomy_vam_set(ctx.ctx, 2)
+    ctx.vam(True)
+    Z.zoomy_model_set(ctx.ctx, 2, Z.friction(0), 9.81, 0.45, 1e-6, 1)  # a new model leaves the VAM mode
+    assert Z.zoomy_nvars(ctx.ctx) == 4
     ctx.close()
