@@ -135,19 +135,21 @@ zoomy_status zoomy_source_mode(zoomy_ctx *ctx, int32_t mode);
 zoomy_status zoomy_space_order(zoomy_ctx *ctx, int32_t order);
 
 /* The non-hydrostatic VAM model in 1D (Sec. "Unsteady Vertically Averaged Momentum Equations in
- * 1D"), flat bed, no friction, as the paper's predictor-corrector splitting (Eq. (PDE-hyperbolic),
- * (PDE-non-hydrostatic), (PDE-non-hydrostatic-update)).  enable = 1 switches a 1D FP64 context
- * (after zoomy_model_set) to the state Q = (h, h u0, h u1, h w0, h w1) (nv = 5, zoomy_nvars); every
- * zoomy_step step is then: predictor Q* by the path-conservative Rusanov scheme for the VAM flux and
- * nonconservative product (dt from s = |u0| + sqrt(g h + u1^2) + |u1|, CFL number of the context,
- * or fixed); corrector: the non-hydrostatic pressure (p0, p1) per cell that makes
- * Q** = Q* - dt S(p), S = (0, d(h p0)/dx, d(h p1)/dx - (3 p0 - p1) dh/dx, -2 p1, 6 (p0 - p1)),
- * satisfy h du0/dx + d(h u1)/dx/3 + u1 dh/dx/3 + 2 w0 = 0 and h du0/dx + u1 dh/dx - 2 w1 = 0 (central
- * differences, mirrored ghosts; a block-tridiagonal linear system, two cells per block, solved on the
- * GPU by cyclic reduction); Q^{n+1} = Q**.  The
- * depth must stay positive (ZOOMY_ENEGDEPTH otherwise).  enable = 0 returns to the level-N model.
- * EINVAL for other contexts, the learned closure, order 2 or the implicit friction mode;
- * zoomy_max_wavespeed and zoomy_lift3d are not defined in this mode (EINVAL). */
+ * 1D"), without friction, over the context's bathymetry b (flat when none was given), as the paper's
+ * predictor-corrector splitting (Eq. (PDE-hyperbolic), (PDE-non-hydrostatic),
+ * (PDE-non-hydrostatic-update)).  enable = 1 switches a 1D FP64 context (after zoomy_model_set) to the
+ * state Q = (h, h u0, h u1, h w0, h w1) (nv = 5, zoomy_nvars), w2 = -(w0 + w1) + (u0 + u1) b_x; every
+ * zoomy_step step is then: predictor Q* by the path-conservative Rusanov scheme with hydrostatic
+ * reconstruction for the VAM flux and nonconservative product (dt from s = |u0| + sqrt(g h + u1^2) +
+ * |u1|, CFL number of the context, or fixed); corrector: the non-hydrostatic pressure (p0, p1) per
+ * cell that makes Q** = Q* - dt S(p), S = (0, d(h p0)/dx + 2 p1 b_x, d(h p1)/dx - (3 p0 - p1) dh/dx -
+ * 6 (p0 - p1) b_x, -2 p1, 6 (p0 - p1)), satisfy h du0/dx + d(h u1)/dx/3 + u1 dh/dx/3 + 2 (w0 - u0 b_x)
+ * = 0 and h du0/dx + u1 dh/dx + 2 (u1 b_x - w1) = 0 (central differences, mirrored ghosts; a
+ * block-tridiagonal linear system, two cells per block, solved on the GPU by cyclic reduction);
+ * Q^{n+1} = Q**.  The depth must stay positive (ZOOMY_ENEGDEPTH otherwise).  enable = 0 returns to the
+ * level-N model, and so does a later zoomy_model_set.  EINVAL for other contexts, enable outside
+ * {0, 1}, the learned closure, order 2 or the implicit friction mode; zoomy_max_wavespeed and
+ * zoomy_lift3d are not defined in this mode (EINVAL). */
 zoomy_status zoomy_vam_set(zoomy_ctx *ctx, int32_t enable);
 
 /* Number of variables nv of the current model. */

@@ -1,16 +1,21 @@
 // vam.cu -- the non-hydrostatic VAM predictor-corrector in 1D (Sec. "Unsteady Vertically Averaged
-// Momentum Equations in 1D"; the splitting of Eq. (PDE-hyperbolic) - Eq. (PDE-source)), FP64, flat bed.
+// Momentum Equations in 1D"; the splitting of Eq. (PDE-hyperbolic) - Eq. (PDE-source)), FP64, over a
+// bed b(x) with b_x the central difference per cell (bed ghosts copy the boundary cell).
 //
-//   Q = (h, h u0, h u1, h w0, h w1), w2 = -(w0 + w1)
-//   predictor: Q* = Q^n - dt/dx (D+_{i-1/2} + D-_{i+1/2}), path-conservative Rusanov fluctuations
-//     D-+ = (F(QR) - F(QL))/2 + Btilde (QR - QL)/2 -+ s_f (QR - QL)/2 with
-//     F = (h u0, h u0^2 + h u1^2/3, 2 h u0 u1, h u0 w0 + h u1 w1/3, h u0 w1 + u1 (h w0 + 2/5 h w2)),
-//     B: row h u0 g h on h; row h u1 -u0 on h u1; row h w1 (w2/5 - w0) on h u1 (3-point Gauss-Legendre
-//     average on the straight segment), s = |u0| + sqrt(g h + u1^2) + |u1|;
+//   Q = (h, h u0, h u1, h w0, h w1), w2 = -(w0 + w1) + (u0 + u1) b_x
+//   predictor: hydrostatic reconstruction per face (b_f = max(b_L, b_R), h* = max(0, h + b - b_f),
+//     velocities kept), Phi = (F(L*) + F(R*))/2 - s_f (R* - L*)/2 with
+//     F = (h u0, h u0^2 + h u1^2/3 + g h^2/2, 2 h u0 u1, h u0 w0 + h u1 w1/3, h u0 w1 + u1 (h w0 + 2/5 h w2)),
+//     the path integral Btilde (R* - L*) of B (row h u1: -u0 on h u1; row h w1: (w2/5 - w0) on h u1) by
+//     3-point Gauss-Legendre on the straight segment, and
+//     Q*_i = Q_i - dt/dx [(Phi - P(h*_i) e1 + Btilde dQ/2)_{i+1/2} - (Phi - P(h*_i) e1 - Btilde dQ/2)_{i-1/2}],
+//     P(h) = g h^2/2, s = |u0| + sqrt(g h* + u1^2) + |u1|; in a flux the cell's own b_x, along a path
+//     the mean of both cells' (a wall ghost's slope changes sign);
 //   corrector: the pressure (p0, p1) per cell such that Q** = Q* - dt S(p),
-//     S = (0, d(h p0)/dx, d(h p1)/dx - (3 p0 - p1) dh/dx, -2 p1, 6 (p0 - p1)),
-//     satisfies R0 = h du0/dx + d(h u1)/dx/3 + u1 dh/dx/3 + 2 w0 = 0 and R1 = h du0/dx + u1 dh/dx - 2 w1 = 0
-//     with central differences and mirrored ghosts (u0, u1 and their momenta change sign at walls).
+//     S = (0, d(h p0)/dx + 2 p1 b_x, d(h p1)/dx - (3 p0 - p1) dh/dx - 6 (p0 - p1) b_x, -2 p1, 6 (p0 - p1)),
+//     satisfies R0 = h du0/dx + d(h u1)/dx/3 + u1 dh/dx/3 + 2 (w0 - u0 b_x) = 0 and
+//     R1 = h du0/dx + u1 dh/dx + 2 (u1 b_x - w1) = 0 with central differences and mirrored ghosts
+//     (u0, u1 and their momenta change sign at walls).
 //
 // The constraints are linear in p with a stencil of two cells on each side.  Grouping two cells per
 // block (unknowns (p0, p1) of cells 2I and 2I+1) makes the system block tridiagonal with 4 x 4 blocks
@@ -44,6 +49,7 @@ constexpr int PCR_ROWS = 8;  // block rows per 128-thread CTA of the reduction
 
 struct VamArgs {
     double *Q;        // state [5][ld] (in: Q^n, out: Q^{n+1})
+    const double *bed;  // b per cell [nc]
     double *Qs;       // predictor result Q* [5][ld]
     double *rows;     // [N][RS] block rows of the pressure system (updated in place by the reduction)
     double *Y[2];     // [N][YS] ping-pong Y of the reduction levels
@@ -64,47 +70,86 @@ __device__ __forceinline__ double vq(const VamArgs &a, const double *Q, int v, i
     return Q[v * a.ld + j];
 }
 
+// b_x of cell j (0 <= j < nc): central difference with copied bed ghosts
+__device__ __forceinline__ double vbx_cell(const VamArgs &a, int64_t j)
+{
+    const int64_t jl = j > 0 ? j - 1 : 0, jr = j + 1 < a.nc ? j + 1 : a.nc - 1;
+    return (a.bed[jr] - a.bed[jl]) * (0.5 / a.dx);
+}
+
+// b and b_x of cell or ghost j (-1 <= j <= nc); a wall ghost's slope changes sign
+__device__ __forceinline__ void vbed(const VamArgs &a, int64_t j, double &b, double &bx)
+{
+    if (j < 0) {
+        b = a.bed[0];
+        bx = a.bcl == 1 ? -vbx_cell(a, 0) : vbx_cell(a, 0);
+    } else if (j >= a.nc) {
+        b = a.bed[a.nc - 1];
+        bx = a.bcr == 1 ? -vbx_cell(a, a.nc - 1) : vbx_cell(a, a.nc - 1);
+    } else {
+        b = a.bed[j];
+        bx = vbx_cell(a, j);
+    }
+}
+
 __device__ __forceinline__ double vspeed(const double *q, double rh, double g)
 {
     const double u0 = q[1] * rh, u1 = q[2] * rh;
     return fabs(u0) + sqrt(g * q[0] + u1 * u1) + fabs(u1);
 }
 
-// F(q); rh = 1 / h (one division per state, the velocities as products)
-__device__ __forceinline__ void vflux(const double *q, double rh, double *F)
+// F(q); rh = 1 / h, or 0 for a dry reconstructed state (the velocities as products)
+__device__ __forceinline__ void vflux(const double *q, double rh, double bx, double g, double *F)
 {
-    const double h = q[0], u0 = q[1] * rh, u1 = q[2] * rh, w0 = q[3] * rh, w1 = q[4] * rh, w2 = -(w0 + w1);
+    const double h = q[0], u0 = q[1] * rh, u1 = q[2] * rh, w0 = q[3] * rh, w1 = q[4] * rh;
+    const double w2 = -(w0 + w1) + (u0 + u1) * bx;
     F[0] = h * u0;
-    F[1] = h * u0 * u0 + h * u1 * u1 / 3.0;
+    F[1] = h * u0 * u0 + h * u1 * u1 / 3.0 + 0.5 * g * h * h;
     F[2] = 2.0 * h * u0 * u1;
     F[3] = h * u0 * w0 + h * u1 * w1 / 3.0;
     F[4] = h * u0 * w1 + u1 * (h * w0 + 0.4 * h * w2);
 }
 
-// Fluctuations of the face between states qL, qR: dm (to the left cell), dp (to the right cell).
-__device__ __forceinline__ void vface(const double *qL, const double *qR, double g, double *dm, double *dp)
+__device__ __forceinline__ double vrh(double h) { return h > 0.0 ? 1.0 / h : 0.0; }
+
+// Face between the states qL, qR over beds (bL, bxL), (bR, bxR): gm to the left cell (its right
+// face), gp to the right cell (its left face).
+__device__ __forceinline__ void vface(const double *qL, const double *qR, double bL, double bxL, double bR,
+                                      double bxR, double g, double *gm, double *gp)
 {
-    double FL[5], FR[5], dq[5], bt[5] = {0, 0, 0, 0, 0};
-    const double rhL = 1.0 / qL[0], rhR = 1.0 / qR[0];
-    vflux(qL, rhL, FL);
-    vflux(qR, rhR, FR);
-    for (int v = 0; v < 5; ++v) dq[v] = qR[v] - qL[v];
+    const double bf = fmax(bL, bR);
+    const double hLs = fmax(0.0, qL[0] + bL - bf), hRs = fmax(0.0, qR[0] + bR - bf);
+    const double fL = qL[0] > 0.0 ? hLs / qL[0] : 0.0, fR = qR[0] > 0.0 ? hRs / qR[0] : 0.0;
+    double Ls[5], Rs[5], FL[5], FR[5], dq[5], bt[5] = {0, 0, 0, 0, 0};
+    Ls[0] = hLs;
+    Rs[0] = hRs;
+    for (int v = 1; v < 5; ++v) {
+        Ls[v] = qL[v] * fL;
+        Rs[v] = qR[v] * fR;
+    }
+    const double rhL = vrh(hLs), rhR = vrh(hRs);
+    vflux(Ls, rhL, bxL, g, FL);
+    vflux(Rs, rhR, bxR, g, FR);
+    for (int v = 0; v < 5; ++v) dq[v] = Rs[v] - Ls[v];
+    const double bxf = 0.5 * (bxL + bxR);
     const double sq[3] = {0.5 - 0.38729833462074168852, 0.5, 0.5 + 0.38729833462074168852};
     const double wq[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
     for (int k = 0; k < 3; ++k) {
         double p[5];
-        for (int v = 0; v < 5; ++v) p[v] = qL[v] + sq[k] * dq[v];
-        const double h = p[0], rh = 1.0 / h, u0 = p[1] * rh, w0 = p[3] * rh, w1 = p[4] * rh, w2 = -(w0 + w1);
-        bt[1] += wq[k] * g * h * dq[0];
+        for (int v = 0; v < 5; ++v) p[v] = Ls[v] + sq[k] * dq[v];
+        const double rh = vrh(p[0]), u0 = p[1] * rh, u1 = p[2] * rh, w0 = p[3] * rh, w1 = p[4] * rh;
+        const double w2 = -(w0 + w1) + (u0 + u1) * bxf;
         bt[2] += wq[k] * (-u0) * dq[2];
         bt[4] += wq[k] * (w2 / 5.0 - w0) * dq[2];
     }
-    const double sL = vspeed(qL, rhL, g), sR = vspeed(qR, rhR, g), sf = sL > sR ? sL : sR;
+    const double sL = vspeed(Ls, rhL, g), sR = vspeed(Rs, rhR, g), sf = sL > sR ? sL : sR;
     for (int v = 0; v < 5; ++v) {
-        const double c = 0.5 * (FR[v] - FL[v]) + 0.5 * bt[v];
-        dm[v] = c - 0.5 * sf * dq[v];
-        dp[v] = c + 0.5 * sf * dq[v];
+        const double phi = 0.5 * (FL[v] + FR[v]) - 0.5 * sf * dq[v];
+        gm[v] = phi + 0.5 * bt[v];
+        gp[v] = phi - 0.5 * bt[v];
     }
+    gm[1] -= 0.5 * g * hLs * hLs;
+    gp[1] -= 0.5 * g * hRs * hRs;
 }
 
 // Programmatic dependent launch: every VAM kernel waits for its predecessor on the stream to complete
@@ -155,24 +200,27 @@ __global__ void __launch_bounds__(128) k_vam_predict(VamArgs a)
         a.ctl->smax_d[a.slot_out] = 0ull;  // the next step's slot
     }
     // a warp per 31 cells: lane j evaluates the face between cells i-1 and i (i = 31 w + j) once;
-    // cell i (j < 31) takes that face's D+ and, from lane j+1, the D- of its right face
+    // cell i (j < 31) takes that face's gp and, from lane j+1, the gm of its right face
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * blockDim.x / 32;
     for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w * 31 < a.nc; w += nw) {
         const int64_t i = 31 * w + lane;
-        double ql[5], qr[5], dm[5], dp[5];
+        double ql[5], qr[5], gm[5], gp[5];
         if (i <= a.nc) {
+            double bL, bxL, bR, bxR;
             for (int v = 0; v < 5; ++v) {
                 ql[v] = vq(a, a.Q, v, i - 1);
                 qr[v] = vq(a, a.Q, v, i);
             }
-            vface(ql, qr, a.g, dm, dp);
+            vbed(a, i - 1, bL, bxL);
+            vbed(a, i, bR, bxR);
+            vface(ql, qr, bL, bxL, bR, bxR, a.g, gm, gp);
         } else {
-            for (int v = 0; v < 5; ++v) qr[v] = dm[v] = dp[v] = 0.0;
+            for (int v = 0; v < 5; ++v) qr[v] = gm[v] = gp[v] = 0.0;
         }
         for (int v = 0; v < 5; ++v) {
-            const double dmr = __shfl_down_sync(0xffffffffu, dm[v], 1);
-            if (lane < 31 && i < a.nc) a.Qs[v * a.ld + i] = qr[v] - dt / a.dx * (dp[v] + dmr);
+            const double gmr = __shfl_down_sync(0xffffffffu, gm[v], 1);  // the right face of cell i
+            if (lane < 31 && i < a.nc) a.Qs[v * a.ld + i] = qr[v] - dt / a.dx * (gmr - gp[v]);
         }
     }
 }
@@ -198,9 +246,10 @@ __device__ __forceinline__ void vcorrected(const VamArgs &a, const Probe &pr, in
     const double dhp0 = (hr * pr.get(jr, 0) - hl * pr.get(jl, 0)) * i2dx;
     const double dhp1 = (hr * pr.get(jr, 1) - hl * pr.get(jl, 1)) * i2dx;
     const double dh = (hr - hl) * i2dx;
+    const double bx = vbx_cell(a, j);
     q[0] = h;
-    q[1] = a.Qs[a.ld + j] - dt * dhp0;
-    q[2] = a.Qs[2 * a.ld + j] - dt * (dhp1 - (3.0 * p0 - p1) * dh);
+    q[1] = a.Qs[a.ld + j] - dt * (dhp0 + 2.0 * p1 * bx);
+    q[2] = a.Qs[2 * a.ld + j] - dt * (dhp1 - (3.0 * p0 - p1) * dh - 6.0 * (p0 - p1) * bx);
     q[3] = a.Qs[3 * a.ld + j] + dt * 2.0 * p1;
     q[4] = a.Qs[4 * a.ld + j] - dt * 6.0 * (p0 - p1);
 }
@@ -222,12 +271,13 @@ __device__ __forceinline__ void vresidual(const VamArgs &a, const Probe &pr, int
         if (a.bcr == 1) qr[1] = -qr[1], qr[2] = -qr[2];
     }
     const double i2dx = 0.5 / a.dx;
-    const double h = qc[0], rh = 1.0 / h, u1 = qc[2] * rh, w0 = qc[3] * rh, w1 = qc[4] * rh;
+    const double h = qc[0], rh = 1.0 / h, u0 = qc[1] * rh, u1 = qc[2] * rh, w0 = qc[3] * rh, w1 = qc[4] * rh;
+    const double bx = vbx_cell(a, i);
     const double dh = (qr[0] - ql[0]) * i2dx;
     const double du0 = (qr[1] / qr[0] - ql[1] / ql[0]) * i2dx;
     const double dhu1 = (qr[2] - ql[2]) * i2dx;
-    R[0] = h * du0 + dhu1 / 3.0 + u1 * dh / 3.0 + 2.0 * w0;
-    R[1] = h * du0 + u1 * dh - 2.0 * w1;
+    R[0] = h * du0 + dhu1 / 3.0 + u1 * dh / 3.0 + 2.0 * (w0 - u0 * bx);
+    R[1] = h * du0 + u1 * dh + 2.0 * (u1 * bx - w1);
 }
 
 // Block rows by probing: thread (i, q) of cell i evaluates R(0) (q = 0, which also writes f = -R(0)
@@ -429,6 +479,7 @@ zoomy_status vam_run_steps(zoomy_ctx *c, double *Q, int64_t ld, double dt, int n
     VamArgs a;
     const int64_t N = (c->nc + 1) / 2;
     a.Q = Q;
+    a.bed = (const double *)c->bed_dev;
     a.Qs = (double *)c->q1;
     a.rows = c->vam_band;
     a.Y[0] = c->vam_band + N * RS;

@@ -1,6 +1,7 @@
 """The VAM predictor-corrector on the GPU (zoomy_vam_set) against the oracle: smooth states with walls
-and with transmissive ends, the standing-wave dispersion against linear wave theory, lake at rest;
-mode checks."""
+and with transmissive ends, flat and over a bed, short and odd lines, the timed workload's size, a
+fixed time step, the standing-wave dispersion against linear wave theory, lake at rest (flat and over
+a hump, bitwise); mode checks."""
 import numpy as np
 import pytest
 
@@ -23,8 +24,8 @@ def Z():
     return zoomy
 
 
-def vam_ctx(Z, n, L, bc):
-    ctx = Z.Context(Z.mesh_1d(n, 0.0, L, bc=bc), 1, Z.friction(0), g=G, cfl=0.45, dtype=1)
+def vam_ctx(Z, n, L, bc, bed=None):
+    ctx = Z.Context(Z.mesh_1d(n, 0.0, L, bc=bc, bathymetry=bed), 1, Z.friction(0), g=G, cfl=0.45, dtype=1)
     ctx.vam(True)
     assert ctx.nv == 5
     return ctx
@@ -55,6 +56,42 @@ def test_matches_oracle(Z, bc):
     assert tg == pytest.approx(tr, rel=1e-12)
     err = rel_l1(got, ref)
     assert np.all(err <= 1e-10), err
+
+
+@pytest.mark.parametrize("bc", [(1, 1), (0, 0), (1, 0)])
+def test_matches_oracle_over_a_bed(Z, bc):
+    """A smooth hump and a ramp under moving water: every b_x term of the predictor and corrector."""
+    n, L, nsteps = 157, 2.0, 25
+    x = (np.arange(n) + 0.5) * L / n
+    bed = 0.25 * np.exp(-((x - 0.7 * L) ** 2) / (0.02 * L * L)) + 0.05 * x / L
+    Q0 = smooth_state(n, L, seed=3 + sum(bc))
+    Q0[0] = Q0[0] - bed
+    for v in range(1, 5):
+        Q0[v] = Q0[v] / (Q0[0] + bed) * Q0[0]
+    ctx = vam_ctx(Z, n, L, bc, bed)
+    Q = to_device(Q0, 1)
+    tg = ctx.step(Q, nsteps=nsteps, dt=0.0)
+    got = Q.cpu().numpy()
+    ctx.close()
+    ref, tr, _ = vam.step(Q0, nsteps, L / n, g=G, bc=bc, cfl=0.45, b=bed)
+    assert tg == pytest.approx(tr, rel=1e-12)
+    err = rel_l1(got, ref)
+    assert np.all(err <= 1e-10), err
+
+
+@pytest.mark.parametrize("bc", [(1, 1), (0, 0)])
+def test_lake_at_rest_over_a_hump_bitwise(Z, bc):
+    n = 96
+    x = (np.arange(n) + 0.5) / n
+    bed = np.round(0.25 * np.exp(-((x - 0.4) ** 2) / 0.01) * 2.0**16) / 2.0**16
+    Q0 = np.zeros((5, n))
+    Q0[0] = 1.0 - bed
+    ctx = vam_ctx(Z, n, 1.0, bc, bed)
+    Q = to_device(Q0, 1)
+    ctx.step(Q, nsteps=40, dt=0.0)
+    got = Q.cpu().numpy()
+    ctx.close()
+    np.testing.assert_array_equal(got, Q0)
 
 
 @pytest.mark.parametrize("n,bc", [(1, (1, 1)), (2, (0, 1)), (3, (1, 0)), (16, (1, 1)), (33, (0, 0))])
