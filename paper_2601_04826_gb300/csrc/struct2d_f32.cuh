@@ -320,13 +320,14 @@ __device__ __forceinline__ void row_body(const StageArgs<float> &a, const RowCtx
     const bool fin = r - 1 >= r0 && r - 1 < r1;  // row r-1 is finished by this step
     float qn[nv];
     if (STAGE == 2) {
-        const float *p = a.Qn + ((fin ? r - 1 : r0) * c.nx + c.csrc);
+        const unsigned o = (unsigned)((fin ? r - 1 : r0) * c.nx + c.csrc);
 #pragma unroll
-        for (int v = 0; v < nv; ++v) qn[v] = p[v * c.ld];
+        for (int v = 0; v < nv; ++v) qn[v] = a.Qn[o + (unsigned)(v * c.ld)];
         if (xrow) {  // bring Q^n of this row into L2; it is read when the row is finished
-            const float *pn = a.Qn + (r * c.nx + c.csrc);
+            const unsigned on = (unsigned)(r * c.nx + c.csrc);
 #pragma unroll
-            for (int v = 0; v < nv; ++v) asm volatile("prefetch.global.L2 [%0];" ::"l"(pn + v * c.ld));
+            for (int v = 0; v < nv; ++v)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(a.Qn + (on + (unsigned)(v * c.ld))));
         }
     }
     // ---- left neighbour (x-face) from the lane on the left, lower neighbour (y-face) from P ----
@@ -417,9 +418,9 @@ __device__ __forceinline__ void row_body(const StageArgs<float> &a, const RowCtx
                 smax = (so > smax || so != so) ? so : smax;
             }
             if (c.owned) {
-                float *o = a.out + ((r - 1) * c.nx + c.col);
+                const unsigned o = (unsigned)((r - 1) * c.nx + c.col);
 #pragma unroll
-                for (int v = 0; v < nv; ++v) o[v * c.ld] = y[v];
+                for (int v = 0; v < nv; ++v) a.out[o + (unsigned)(v * c.ld)] = y[v];
             }
         }
     }
