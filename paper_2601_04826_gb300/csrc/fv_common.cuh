@@ -89,6 +89,31 @@ __device__ __forceinline__ void step_bookkeeping(const StageArgs<T> &a, T dt)
         a.ctl->smax_d[a.slot_out] = 0ull;
 }
 
+// Programmatic dependent launch: a kernel launched with launch_pdl waits here for its predecessor on
+// the stream to complete (with its memory visible), then lets the next kernel launch, so each launch
+// and CTA ramp overlaps the kernel before it.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+static inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 template <typename T>
 __device__ __forceinline__ void reduce_smax(DevCtl *ctl, int slot, T s)
 {

@@ -44,6 +44,7 @@ template <int N, typename T, int STAGE>
 __global__ void __launch_bounds__(256) k_stage_1d(StageArgs<T> a)
 {
     constexpr int m = N + 1, nv = 1 + m;
+    pdl_enter();
     if (*(volatile unsigned int *)&a.ctl->status) return;
     T dt;
     if (!step_dt(a, dt)) {
@@ -295,13 +296,11 @@ static cudaError_t launch_1d(const StageArgs<T> &a, int stage, cudaStream_t st)
 {
     // small lines (the work is FP64-rate bound, not memory bound): one-warp CTAs spread the cells
     // over as many SMs as possible; large lines use 256-thread CTAs
+    // (programmatic dependent launch: each stage's launch overlaps the previous kernel's tail)
     const int bs = a.nx < 65536 ? 32 : 256;
     dim3 grid((a.nx + bs - 1) / bs), block(bs);
-    if (stage == 1)
-        k_stage_1d<N, T, 1><<<grid, block, 0, st>>>(a);
-    else
-        k_stage_1d<N, T, 2><<<grid, block, 0, st>>>(a);
-    return cudaGetLastError();
+    if (stage == 1) return launch_pdl(k_stage_1d<N, T, 1>, grid, block, st, a);
+    return launch_pdl(k_stage_1d<N, T, 2>, grid, block, st, a);
 }
 
 template <int N, typename T>

@@ -152,15 +152,6 @@ __device__ __forceinline__ void vface(const double *qL, const double *qR, double
     gp[1] -= 0.5 * g * hRs * hRs;
 }
 
-// Programmatic dependent launch: every VAM kernel waits for its predecessor on the stream to complete
-// (with its memory visible), then lets the next kernel launch, so each launch and CTA ramp overlaps
-// the kernel before it.
-__device__ __forceinline__ void pdl_enter()
-{
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
 __device__ __forceinline__ double vam_dt(const VamArgs &a)
 {
     if (a.dt_fixed > 0.0) return a.dt_fixed;
@@ -456,22 +447,6 @@ __global__ void __launch_bounds__(128) k_vam_correct(VamArgs a)
         if (q[0] <= 0.0) flag |= DEV_NEGDEPTH;
     }
     if (flag) atomicOr(&a.ctl->status, flag);
-}
-
-template <typename... KArgs, typename... Args>
-static cudaError_t launch_pdl(void (*k)(KArgs...), unsigned grid, unsigned block, cudaStream_t st, Args... args)
-{
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k, args...);
 }
 
 zoomy_status vam_run_steps(zoomy_ctx *c, double *Q, int64_t ld, double dt, int nsteps)
