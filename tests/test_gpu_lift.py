@@ -106,3 +106,18 @@ def test_lift_argument_checks(Z):
     o = out[:8].cpu().numpy().reshape(4, 2, 64)
     assert np.all(o[:3] == 0.0) and np.allclose(o[3, 0], G) and np.all(o[3, 1] == 0.0)
     ctx.close()
+
+
+def test_lift_full_size(Z, oracle):
+    """The timed lifting workload's size and launch configuration: 2048^2 level 2, FP32, 16 sigma levels,
+    a moving state over the bench's bathymetry; every output against the oracle."""
+    level, n = 2, 2048
+    _, bed = inputs.gaussian_bump_2d(n, n, level, seed=0)
+    Q = inputs.random_moments_2d(n, n, level, seed=8, vel=0.3)
+    Qr, bedr = rounded(Q, 0), rounded(bed, 0)
+    zeta = np.linspace(0.0, 1.0, 16)
+    ctx = Z.Context(Z.mesh_2d(n, n, bathymetry=bedr), level, Z.friction(1, C=0.1, nu=0.01), dtype=0)
+    got = lift_gpu(Z, ctx, Qr, 0, zeta=zeta)
+    ctx.close()
+    ref = oracle.lift3d(oracle.Model(level, 2, g=G), oracle.Mesh.rect(n, n, 0, 1, 0, 1), Qr, zeta, bed=bedr)
+    check(got, ref, 2e-5)

@@ -115,3 +115,30 @@ def test_order_checks(Z):
     with pytest.raises(Z.ZoomyError):
         Z.zoomy_closure_set(ctx.ctx, np.zeros(4998), np.ones(6), np.ones(6), 0.1)
     ctx.close()
+
+
+def test_full_size_order2(Z, oracle):
+    """The timed second-order workload's size and launch configuration: 2048^2 level 2, FP32, the bench's
+    bathymetry and surface bump with a background flow and non-zero moments, two steps at CFL 0.45,
+    against the oracle's FP32-state form and its FP64 form."""
+    n, level = 2048, 2
+    Q0, bed = inputs.gaussian_bump_2d(n, n, level, seed=0)
+    h = Q0[0]
+    for v, a in [(1, 0.3), (2, -0.2), (3, 0.1), (4, -0.05), (5, 0.05), (6, 0.02)]:
+        Q0[v] = h * a
+    Qr, bedr = rounded(Q0, 0), rounded(bed, 0)
+    ctx = Z.Context(Z.mesh_2d(n, n, bathymetry=bedr), level, Z.friction(1, C=0.1, nu=0.01), cfl=0.45, dtype=0)
+    Z.zoomy_space_order(ctx.ctx, 2)
+    Q = to_device(Qr, 0)
+    tg = ctx.step(Q, nsteps=2, dt=0.0)
+    got = Q.double().cpu().numpy()
+    ctx.close()
+    md = oracle.Model(level, 2, g=G, h_dry=1e-6, friction=1, C=0.1, nu=0.01, order=2)
+    omesh = oracle.Mesh.rect(n, n, 0, 1, 0, 1, bc=(1, 1, 1, 1))
+    ref32, tr = oracle.step(md, omesh, Qr, 2, dt=0.0, cfl=0.45, bed=bedr, store_f32=True)
+    ref64, _ = oracle.step(md, omesh, Qr, 2, dt=0.0, cfl=0.45, bed=bedr)
+    err32, err64 = rel_l1(got, ref32), rel_l1(got, ref64)
+    print("relative L1 vs FP32-storage oracle", err32, "vs FP64 oracle", err64)
+    assert tg == pytest.approx(tr, rel=1e-5)
+    assert np.all(err32 <= 1e-5), err32
+    assert np.all(err64 <= 1e-5), err64
