@@ -161,3 +161,21 @@ def test_engines_agree(Z):
     assert np.all(np.isfinite(a)) and np.all(np.isfinite(b))
     rel = np.linalg.norm(a - b) / np.linalg.norm(b)
     assert rel < 2e-3, rel
+
+
+def test_random_network_full_size(Z, oracle):
+    """The closure workload's size and launch configuration: 1024^2, the tcgen05 engine, a full network,
+    two steps, against the oracle's closed level-4 solver with BF16 layer inputs."""
+    n = 1024
+    Q0, bed = state(n, n, 17)
+    rng = np.random.default_rng(19)
+    p = mlp.init_params(21)
+    for k in p:
+        p[k] = 0.5 * p[k] + 0.02 * rng.normal(size=p[k].shape)
+    ins = np.array([1.0, 2.0, 2.0, 4.0, 4.0, 5.0])
+    outs = np.full(6, 0.05)
+    got, ref, tg, tr = run_closure(Z, oracle, mlp.pack(p), ins, outs, n, n, 2, Q0, bed, bc=(1, 1, 1, 1), engine=0)
+    err = rel_l1(got, ref)
+    print("closed solver relative L1 at 1024^2", err)
+    assert tg == pytest.approx(tr, rel=1e-4)
+    assert np.all(err <= 1e-4), err
