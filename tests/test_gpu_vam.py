@@ -197,3 +197,29 @@ def test_mode_checks(Z):
     Z.zoomy_model_set(ctx.ctx, 2, Z.friction(0), 9.81, 0.45, 1e-6, 1)  # a new model leaves the VAM mode
     assert Z.zoomy_nvars(ctx.ctx) == 4
     ctx.close()
+
+
+def test_long_line_properties(Z):
+    """131072 cells (128-thread CTAs, capped grids, grid-stride loops, 16 reduction levels), beyond the
+    oracle's dense solve: properties that hold at any size.  Between walls the mass is conserved, and
+    the corrected state satisfies both constraints: R0 and R1 evaluated on it by the oracle's
+    residual (central differences, the same ghosts) vanish to round-off relative to their terms."""
+    n, L = 131072, 400.0
+    dx = L / n
+    x = (np.arange(n) + 0.5) * dx
+    bed = 0.2 * np.exp(-((x - 0.6 * L) ** 2) / 200.0)
+    Q0 = np.zeros((5, n))
+    Q0[0] = 1.0 + 0.1 * np.exp(-((x - 0.3 * L) ** 2) / 50.0) - bed
+    Q0[1] = 0.1 * Q0[0] * np.sin(2 * np.pi * x / L)
+    ctx = vam_ctx(Z, n, L, (1, 1), bed)
+    Q = to_device(Q0, 1)
+    ctx.step(Q, nsteps=3, dt=0.0)
+    got = Q.cpu().numpy()
+    ctx.close()
+    assert np.all(np.isfinite(got))
+    assert abs(got[0].sum() - Q0[0].sum()) / Q0[0].sum() < 1e-13
+    bx = vam.bed_slope(bed, dx, (1, 1))[0]
+    R = vam.residual(got, np.zeros(2 * n), 0.0, dx, (1, 1), bx)
+    h, u0, u1, w0, w1, _ = vam.prim(got)
+    scale = np.abs(h * vam.diff(u0, dx, (1, 1), True)).max() + 2.0 * np.abs(w0).max() + 2.0 * np.abs(w1).max()
+    assert np.abs(R).max() <= 1e-9 * scale, (np.abs(R).max(), scale)
