@@ -7,9 +7,12 @@ C = 0.1 with Newtonian nu = 0.01, adaptive CFL 0.45 step computed on the device.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
---impl reference times the FP64 CPU oracle (the baseline of this port) on the host cores on a
-bounded window of the same workload.  For N > 1 (torchrun) every rank runs an independent replica
-of the workload (the step has no data-parallel split on one grid in this build): weak scaling.
+--impl reference times the FP64 CPU oracle (the reference arm) on the host cores on a bounded
+window of the same workload.  For N > 1 (torchrun) every rank runs an independent replica of the
+workload (one grid is not split across GPUs): weak scaling.
+
+Other workloads print their own lines: --workload tri | ensemble | closure | closure-kernels |
+dambreak1d | lift | vam.
 """
 from __future__ import annotations
 
