@@ -456,10 +456,10 @@ zoomy_status vam_run_steps(zoomy_ctx *c, double *Q, int64_t ld, double dt, int n
     a.Q = Q;
     a.bed = (const double *)c->bed_dev;
     a.Qs = (double *)c->q1;
-    a.rows = c->vam_band;
-    a.Y[0] = c->vam_band + N * RS;
+    a.rows = c->vam_sys;
+    a.Y[0] = c->vam_sys + N * RS;
     a.Y[1] = a.Y[0] + N * YS;
-    a.rhs = c->vam_rhs;
+    a.rhs = c->vam_p;
     a.ld = ld;
     a.nc = c->nc;
     a.dx = c->dx;
@@ -513,10 +513,10 @@ extern "C" zoomy_status zoomy_vam_set(zoomy_ctx *c, int32_t enable)
             return set_error(ZOOMY_EINVAL, "zoomy_vam_set: needs a 1D FP64 context after zoomy_model_set");
         if (c->closure_on || c->order != 1 || c->src_implicit)
             return set_error(ZOOMY_EINVAL, "zoomy_vam_set: not with the closure, order 2 or implicit friction");
-        if (!c->vam_band) {
+        if (!c->vam_sys) {
             const size_t N = (size_t)(c->nc + 1) / 2;
-            cudaError_t e = cudaMalloc(&c->vam_band, sizeof(double) * N * (RS + 2 * YS));
-            if (e == cudaSuccess) e = cudaMalloc(&c->vam_rhs, sizeof(double) * 4 * N);
+            cudaError_t e = cudaMalloc(&c->vam_sys, sizeof(double) * N * (RS + 2 * YS));
+            if (e == cudaSuccess) e = cudaMalloc(&c->vam_p, sizeof(double) * 4 * N);
             if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
         }
         c->vam = 1;

@@ -116,8 +116,8 @@ extern "C" zoomy_status zoomy_mesh_destroy(zoomy_ctx *c)
     cudaFree(c->qdev_host);
     cudaFree(c->closure_d);
     cudaFree(c->closure_pred);
-    cudaFree(c->vam_band);
-    cudaFree(c->vam_rhs);
+    cudaFree(c->vam_sys);
+    cudaFree(c->vam_p);
     cudaFree(c->closure_tc);
     for (cudaEvent_t ev : c->prof_events) cudaEventDestroy(ev);
     tri_free(c);

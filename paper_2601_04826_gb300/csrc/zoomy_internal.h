@@ -34,7 +34,7 @@ struct zoomy_ctx {
     int src_implicit = 0;  // 0: explicit Newtonian + implicit bottom stress; 1: friction fully implicit
     int order = 1;         // space order: 1, or 2 (MUSCL, fv_order2.cu; 1D and structured 2D)
     int vam = 0;           // 1: the non-hydrostatic VAM predictor-corrector (vam.cu), 1D FP64
-    double *vam_band = nullptr, *vam_rhs = nullptr;  // its banded pressure system
+    double *vam_sys = nullptr, *vam_p = nullptr;  // its pressure system (block rows, reduction arrays), p
     // device buffers owned by the context
     void *bed_dev = nullptr;
     void *q1 = nullptr;
