@@ -328,16 +328,19 @@ zoomy_status zoomy_profile_read(zoomy_ctx *ctx, int64_t *launches, double *total
  * y-, y+}) with the FP32 state path of zoomy_step: Q is the caller's device state [nv][ld]
  * (nv = 2 level + 3, ld >= nx ny), bed the caller's device bed level [nx ny] (required; zeros for a
  * flat bed), and the other arguments mean what they mean for zoomy_mesh_create / zoomy_model_set /
- * zoomy_step.  The stage buffer and the step's control block live in one array of
- * ZOOMY_NOALLOC_SCRATCH_BYTES compiled into the library, reserved on every GPU that loads it until
- * the process exits: a state needing more (256 + 4 nv ld bytes) is rejected with ZOOMY_EINVAL and
- * a message naming the limit, before any device work.  The call allocates nothing (no cudaMalloc,
- * no cudaFree, no allocating library routine); it clears the control block it needs zeroed at its
- * start, because the array keeps the previous call's contents.  All calls share that one array:
- * calls whose device work overlaps (other streams or threads, without ordering) race on it.  The
- * first call on each device looks up the array's device address with that device current; make that
- * first call before any stream capture.  t_advanced != NULL synchronises the stream and reports
- * device-detected errors as zoomy_step does. */
+ * zoomy_step (the same friction parameters are refused).  Q and bed must be float-aligned, and
+ * nx ny must fit a 32-bit cell index.  The stage buffer and the step's control block live in one
+ * array of ZOOMY_NOALLOC_SCRATCH_BYTES compiled into the library, reserved on every GPU that loads
+ * it until the process exits: a state needing more (256 + 4 nv ld bytes) is rejected with
+ * ZOOMY_EINVAL and a message naming the limit.  Every rejection happens before any device work.
+ * The call allocates nothing (no cudaMalloc, no cudaFree, no allocating library routine); it clears
+ * the control block it needs zeroed at its start, because the array keeps the previous call's
+ * contents.  All calls share that one array: calls whose device work overlaps (other streams or
+ * threads, without ordering) race on it.  Every call looks up the array's device address on the
+ * current device (so a device reset between calls is harmless); the first call on a device also
+ * loads the library's device code there, so make that first call before any stream capture.
+ * t_advanced != NULL synchronises the stream and reports device-detected errors as zoomy_step
+ * does; with t_advanced == NULL nothing is read back. */
 zoomy_status zoomy_step_noalloc(int64_t nx, int64_t ny, double x0, double x1, double y0, double y1,
                                 const int32_t *bc, int32_t level, const zoomy_friction *friction, double g,
                                 double cfl, double h_dry, const float *bed, float *Q, int64_t ld, double dt,

@@ -9,7 +9,6 @@
 // process exits, which is why its size is capped at ZOOMY_NOALLOC_SCRATCH_BYTES.
 #include <cstdint>
 #include <cstring>
-#include <mutex>
 
 #include <cuda_runtime.h>
 
@@ -29,28 +28,23 @@ static_assert(sizeof(DevCtl) <= kCtlBytes, "control block must fit its slot");
 // The shared scratch: [DevCtl | stage buffer Q1].  Host code must not use this name as an address.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void *g_scratch_dev[kMaxDevices] = {};  // device address of g_noalloc_scratch, per device
-int g_nsm[kMaxDevices] = {};
-
-// Once per device, with that device current: look up the device address of the scratch array.
-zoomy_status scratch_setup(int dev, void **ptr, int *nsm)
+// Look up the device address of the scratch array on the current device.  This runs on every
+// call: the lookup allocates nothing, and an address cached across calls would dangle after a
+// cudaDeviceReset (the library's device code is loaded again, possibly elsewhere).  The first call
+// on a device loads that device code.
+zoomy_status scratch_setup(void **ptr, int *nsm)
 {
-    if (dev < 0 || dev >= kMaxDevices) return set_error(ZOOMY_EINVAL, "zoomy_step_noalloc: device %d out of range", dev);
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_dev[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) return cuda_fail(e == cudaSuccess ? cudaErrorInvalidSymbol : e, "cudaGetSymbolAddress");
-        int n = 0;
-        e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
-        g_scratch_dev[dev] = p;
-        g_nsm[dev] = n;
-    }
-    *ptr = g_scratch_dev[dev];
-    *nsm = g_nsm[dev];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(e == cudaSuccess ? cudaErrorInvalidSymbol : e, "cudaGetSymbolAddress");
+    int n = 0;
+    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    *ptr = p;
+    *nsm = n > 0 ? n : 1;
     return ZOOMY_OK;
 }
 
@@ -72,30 +66,33 @@ extern "C" zoomy_status zoomy_step_noalloc(int64_t nx, int64_t ny, double x0, do
         return set_error(ZOOMY_EINVAL, "%s: need g > 0, 0 < cfl <= 1, h_dry >= 0, dt >= 0, nsteps >= 0", who);
     zoomy_friction f = {ZOOMY_FRICTION_NONE, 0.0, 0.0, 1.0, 0.0};
     if (friction) f = *friction;
-    if (f.kind < 0 || f.kind > 2 || !(f.rho > 0.0)) return set_error(ZOOMY_EINVAL, "%s: bad friction", who);
+    if (!friction_ok(f)) return set_error(ZOOMY_EINVAL, "%s: bad friction parameters", who);
+    // the kernels index cells with 32-bit integers: reject sizes whose products would wrap
+    if (nx > INT32_MAX || ny > INT32_MAX || nx > INT32_MAX / ny)
+        return set_error(ZOOMY_EINVAL, "%s: nx = %lld, ny = %lld exceed the 32-bit cell index", who, (long long)nx,
+                         (long long)ny);
     const int64_t nc = nx * ny;
     const int nv = 2 * level + 3;
     if (ld < nc) return set_error(ZOOMY_EINVAL, "%s: ld < nx * ny", who);
+    if (((uintptr_t)Q) % sizeof(float) || ((uintptr_t)bed) % sizeof(float))
+        return set_error(ZOOMY_EINVAL, "%s: Q and bed must be 4-byte aligned float arrays", who);
     // the stage buffer has the caller's layout [nv][ld] and must fit the fixed scratch
-    const size_t need = kCtlBytes + sizeof(float) * (size_t)nv * (size_t)ld;
-    if (need > kScratchBytes || (int64_t)nv * ld >= (1LL << 31))
+    if (ld > (int64_t)(kScratchBytes / sizeof(float)) ||
+        kCtlBytes + sizeof(float) * (size_t)nv * (size_t)ld > kScratchBytes)
         return set_error(ZOOMY_EINVAL,
                          "%s: state of %d x %lld floats needs %zu bytes of scratch; the fixed scratch holds %zu "
                          "(use zoomy_step for larger grids)",
-                         who, nv, (long long)ld, need, kScratchBytes);
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+                         who, nv, (long long)ld, kCtlBytes + sizeof(float) * (size_t)nv * (size_t)ld, kScratchBytes);
     void *scratch = nullptr;
     int nsm = 1;
-    zoomy_status st = scratch_setup(dev, &scratch, &nsm);
+    zoomy_status st = scratch_setup(&scratch, &nsm);
     if (st != ZOOMY_OK) return st;
     DevCtl *ctl = (DevCtl *)scratch;
     float *Q1 = (float *)((char *)scratch + kCtlBytes);
     cudaStream_t s = (cudaStream_t)stream;
 
     // the control block keeps the previous call's contents: clear it (wave-speed slots, time, status)
-    e = cudaMemsetAsync(ctl, 0, sizeof(DevCtl), s);
+    cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(DevCtl), s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     StageArgs<float> a;
     memset(&a, 0, sizeof(a));

@@ -163,8 +163,7 @@ extern "C" zoomy_status zoomy_model_set(zoomy_ctx *c, int32_t level, const zoomy
     if (dtype != ZOOMY_FP32 && dtype != ZOOMY_FP64) return set_error(ZOOMY_EINVAL, "zoomy_model_set: bad dtype");
     zoomy_friction f = {ZOOMY_FRICTION_NONE, 0.0, 0.0, 1.0, 0.0};
     if (fr) f = *fr;
-    if (f.kind < 0 || f.kind > 2 || !(f.rho > 0.0) || f.C < 0.0 || f.nu < 0.0 || f.manning_n < 0.0)
-        return set_error(ZOOMY_EINVAL, "zoomy_model_set: bad friction parameters");
+    if (!friction_ok(f)) return set_error(ZOOMY_EINVAL, "zoomy_model_set: bad friction parameters");
     if (c->kind == ZOOMY_MESH_TRI && dtype != ZOOMY_FP32)
         return set_error(ZOOMY_EINVAL, "zoomy_model_set: triangle meshes run the FP32 state path");
     c->level = level;

@@ -87,6 +87,12 @@ zoomy_status read_status(zoomy_ctx *c, double *t_total);
 // record a profiling event before / after a stage launch (no-op when profiling is off)
 zoomy_status prof_mark(zoomy_ctx *c, int stage, bool start);
 zoomy_status check_step_args(zoomy_ctx *c, const void *Q, int64_t ld, double dt, int32_t nsteps, const char *who);
+// friction parameters accepted by zoomy_model_set and zoomy_step_noalloc: a known kind, rho > 0 and
+// C, nu, manning_n >= 0 (negative values would run as anti-damping)
+inline bool friction_ok(const zoomy_friction &f)
+{
+    return f.kind >= 0 && f.kind <= 2 && f.rho > 0.0 && f.C >= 0.0 && f.nu >= 0.0 && f.manning_n >= 0.0;
+}
 // triangle meshes (fv_tri.cu)
 zoomy_status create_tri_mesh(const zoomy_mesh_desc *d, void *stream, zoomy_ctx **out);
 void tri_free(zoomy_ctx *c);

@@ -14,6 +14,19 @@ def rel_l1(got, ref):
     return np.array(out)
 
 
+def rel_max(got, ref):
+    """Per-variable element-wise error max|got - ref| / max|ref| (absolute where ref is ~0): a wrong
+    cell, a bad corner or a wrong ghost column shows here even when it is lost in a global L1 norm."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    out = []
+    for v in range(ref.shape[0]):
+        den = np.abs(ref[v]).max() if ref.shape[1] else 0.0
+        num = np.abs(got[v] - ref[v]).max() if ref.shape[1] else 0.0
+        out.append(num / den if den > 1e-300 else num)
+    return np.array(out)
+
+
 def to_device(Q, dtype):
     import torch
 

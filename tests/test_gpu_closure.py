@@ -10,7 +10,7 @@
 import numpy as np
 import pytest
 
-from gpu_util import rel_l1, rounded, to_device
+from gpu_util import rel_l1, rel_max, rounded, to_device
 from oracle import mlp
 from paper_2601_04826_gb300 import inputs
 
@@ -175,7 +175,10 @@ def test_random_network_full_size(Z, oracle):
     ins = np.array([1.0, 2.0, 2.0, 4.0, 4.0, 5.0])
     outs = np.full(6, 0.05)
     got, ref, tg, tr = run_closure(Z, oracle, mlp.pack(p), ins, outs, n, n, 2, Q0, bed, bc=(1, 1, 1, 1), engine=0)
-    err = rel_l1(got, ref)
-    print("closed solver relative L1 at 1024^2", err)
+    err, emax = rel_l1(got, ref), rel_max(got, ref)
+    print("closed solver relative L1 at 1024^2", err, "element-wise", emax)
     assert tg == pytest.approx(tr, rel=1e-4)
     assert np.all(err <= 1e-4), err
+    # a layer input that sits at a BF16 rounding tie on one side only moves one predicted moment by
+    # one BF16 step (2^-8 relative) in that cell: bounded per cell by 1e-3 of each variable's size
+    assert np.all(emax <= 1e-3), emax

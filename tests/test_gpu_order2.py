@@ -5,7 +5,7 @@ argument checks."""
 import numpy as np
 import pytest
 
-from gpu_util import rel_l1, rounded, to_device
+from gpu_util import rel_l1, rel_max, rounded, to_device
 from paper_2601_04826_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -138,7 +138,11 @@ def test_full_size_order2(Z, oracle):
     ref32, tr = oracle.step(md, omesh, Qr, 2, dt=0.0, cfl=0.45, bed=bedr, store_f32=True)
     ref64, _ = oracle.step(md, omesh, Qr, 2, dt=0.0, cfl=0.45, bed=bedr)
     err32, err64 = rel_l1(got, ref32), rel_l1(got, ref64)
+    emax32, emax64 = rel_max(got, ref32), rel_max(got, ref64)
     print("relative L1 vs FP32-storage oracle", err32, "vs FP64 oracle", err64)
+    print("element-wise vs FP32-storage oracle", emax32, "vs FP64 oracle", emax64)
     assert tg == pytest.approx(tr, rel=1e-5)
     assert np.all(err32 <= 1e-5), err32
     assert np.all(err64 <= 1e-5), err64
+    assert np.all(emax32 <= 1e-5), emax32
+    assert np.all(emax64 <= 1e-5), emax64

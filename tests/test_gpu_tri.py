@@ -4,7 +4,7 @@ triangles.  The library's cells are in its own order: zoomy_mesh_permutation map
 import numpy as np
 import pytest
 
-from gpu_util import rel_l1, rounded, to_device
+from gpu_util import rel_l1, rel_max, rounded, to_device
 from paper_2601_04826_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -101,9 +101,9 @@ def test_tri_full_size_config3(Z, oracle):
     assert len(tris) > 3.9e6
     Q0 = inputs.circular_dam_tri(verts, tris, level, radius=0.2, h_in=1.5)
     got, ref32, tg, tr = run_tri(Z, oracle, verts, tris, level, Q0, 2, store_f32=True)
-    err = rel_l1(got, ref32)
-    print("relative L1 vs FP32-storage oracle", err)
-    assert err[0] <= 1e-5
-    # the momenta start at rest inside a dry domain; bound them against their own scale
-    scale = np.abs(ref32[1:]).max()
-    assert np.abs(got[1:] - ref32[1:]).max() <= 1e-4 * scale
+    err, emax = rel_l1(got, ref32), rel_max(got, ref32)
+    print("relative L1 vs FP32-storage oracle", err, "element-wise", emax)
+    worst = np.argmax(np.abs(got - ref32), axis=1)
+    print("worst cells", worst, "h there", ref32[0, worst], "got", got[0, worst])
+    assert np.all(err <= 1e-5), err
+    assert np.all(emax <= 1e-5), emax
