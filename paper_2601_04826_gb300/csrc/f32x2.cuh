@@ -3,7 +3,6 @@
 // Blackwell executes FADD2 / FMUL2 / FFMA2 on a pair of FP32 values per lane and instruction.
 // The structured-grid kernels evaluate the x-face and the y-face of a cell as the two halves of
 // one pair, so every arithmetic step of the face term costs one instruction for both faces.
-// Subtraction goes through sub.rn.f32x2 so that no operand needs a separate negation.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -18,12 +17,6 @@ struct F2 {
     __device__ __forceinline__ float y() const { return v.y; }
 };
 
-__device__ __forceinline__ F2 mk2(float2 a)
-{
-    F2 r;
-    r.v = a;
-    return r;
-}
 __device__ __forceinline__ unsigned long long as_u64(F2 a)
 {
     return (unsigned long long)__float_as_uint(a.v.x) | ((unsigned long long)__float_as_uint(a.v.y) << 32);
@@ -32,8 +25,23 @@ __device__ __forceinline__ F2 from_u64(unsigned long long u)
 {
     return F2(__uint_as_float((unsigned)u), __uint_as_float((unsigned)(u >> 32)));
 }
-__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return mk2(__fadd2_rn(a.v, b.v)); }
-__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return mk2(__fmul2_rn(a.v, b.v)); }
+// Every packed operation is written as PTX with an explicit rounding modifier.  The compiler can
+// neither split such an instruction into scalar halves (it may do that with the equivalent
+// intrinsics when one half of a result is unused) nor contract a .rn multiply into a later addition,
+// so an expression rounds the same way wherever it is inlined.  The stage kernels rely on this for
+// results that are bitwise independent of the row decomposition.
+__device__ __forceinline__ F2 operator+(F2 a, F2 b)
+{
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(as_u64(a)), "l"(as_u64(b)));
+    return from_u64(d);
+}
+__device__ __forceinline__ F2 operator*(F2 a, F2 b)
+{
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(as_u64(a)), "l"(as_u64(b)));
+    return from_u64(d);
+}
 __device__ __forceinline__ F2 operator-(F2 a, F2 b)
 {
     unsigned long long d;
@@ -41,7 +49,11 @@ __device__ __forceinline__ F2 operator-(F2 a, F2 b)
     return from_u64(d);
 }
 // a * b + c
-__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) { return mk2(__ffma2_rn(a.v, b.v, c.v)); }
-__device__ __forceinline__ F2 max2(F2 a, F2 b) { return F2(fmaxf(a.v.x, b.v.x), fmaxf(a.v.y, b.v.y)); }
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(as_u64(a)), "l"(as_u64(b)), "l"(as_u64(c)));
+    return from_u64(d);
+}
 
 }  // namespace zoomy

@@ -45,6 +45,7 @@ static cudaError_t launch_f32(const StageArgs<float> &a, int stage, int wpb, cud
 {
     (void)wpb;  // one warp per CTA
     if (!a.bed) return cudaErrorInvalidValue;
+    if (stage == 2 && a.Qn != a.out) return cudaErrorInvalidValue;  // stage 2 updates Q^n in place
     dim3 grid(a.nstrips * a.nsegs), block(32);
     if (a.src_implicit) {
         if (stage == 1)

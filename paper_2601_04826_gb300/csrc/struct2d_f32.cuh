@@ -79,7 +79,10 @@ __device__ __forceinline__ void make_side(Side2<N> &r, float h, float b, const f
                 if constexpr (w != 0.0) {
                     if constexpr (j >= i) {
                         constexpr double w2 = (i == j) ? w : 2.0 * w;
-                        sq = fma2(F2(float(w2)) * r.n[i], r.n[j], sq);
+                        if constexpr (w2 == 1.0)
+                            sq = fma2(r.n[i], r.n[j], sq);
+                        else
+                            sq = fma2(F2(float(w2)) * r.n[i], r.n[j], sq);
                     }
                     sab = fmaf(float(w) * a[i], c[j], sab);
                 }
@@ -250,7 +253,7 @@ __device__ __forceinline__ void friction32(float h, float *ya, float *yb, int fr
     }
     const float dc = dt * c;
     const float f = dc * rcpa(fmaf(dc, float(m * m), 1.0f));
-    const float fa = f * sa, fb = f * sb;
+    const float fa = __fmul_rn(f, sa), fb = __fmul_rn(f, sb);  // never contracted into the update below
 #pragma unroll
     for (int k = 0; k < m; ++k) {
         ya[k] = wet ? fmaf(-float(2 * k + 1), fa, ya[k]) : 0.0f;
@@ -278,7 +281,7 @@ __device__ __forceinline__ void load_row(const StageArgs<float> &a, const RowCtx
 
 // Process row r with the previous row state P and the current row state C.  IMP: the friction
 // (bulk + bottom stress) by backward Euler after the stage instead of the default treatment.
-template <int N, int STAGE, bool IMP = false>
+template <int N, int STAGE, bool IMP = false, bool STEADY = false>
 __device__ __forceinline__ void row_body(const StageArgs<float> &a, const RowCtx &c, int r, int r0, int r1, float dt,
                                          float *nxt, RowState<N> &P, RowState<N> &C, float &smax, unsigned &flag)
 {
@@ -315,30 +318,38 @@ __device__ __forceinline__ void row_body(const StageArgs<float> &a, const RowCtx
         });
     }
     // ---- prefetch the next row, and Q^n of the row finished in this step --------------------
-    if (r < r1) load_row<N, STAGE>(a, c, r + 1, nxt);
-    const bool xrow = r >= r0 && r < r1;
-    const bool fin = r - 1 >= r0 && r - 1 < r1;  // row r-1 is finished by this step
+    // STEADY: a row strictly inside the segment (r0 < r < r1): every flag below is true
+    if (STEADY || r < r1) load_row<N, STAGE>(a, c, r + 1, nxt);
+    const bool xrow = STEADY || (r >= r0 && r < r1);
+    const bool fin = STEADY || (r - 1 >= r0 && r - 1 < r1);  // row r-1 is finished by this step
+    // Stage 2 updates Q^n in place (the launcher checks out == Qn): Q^n of the finished row is read
+    // from the addresses its result is stored to.
     float qn[nv];
+    float *const orow = a.out + (unsigned)((fin ? r - 1 : r0) * c.nx + c.csrc);
     if (STAGE == 2) {
-        const unsigned o = (unsigned)((fin ? r - 1 : r0) * c.nx + c.csrc);
 #pragma unroll
-        for (int v = 0; v < nv; ++v) qn[v] = a.Qn[o + (unsigned)(v * c.ld)];
+        for (int v = 0; v < nv; ++v) qn[v] = orow[(unsigned)(v * c.ld)];
         if (xrow) {  // bring Q^n of this row into L2; it is read when the row is finished
-            const unsigned on = (unsigned)(r * c.nx + c.csrc);
 #pragma unroll
             for (int v = 0; v < nv; ++v)
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(a.Qn + (on + (unsigned)(v * c.ld))));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(orow + (unsigned)(c.nx + v * c.ld)));
         }
     }
     // ---- left neighbour (x-face) from the lane on the left, lower neighbour (y-face) from P ----
     // Ln/Lt/Lgnn/Lgnt carry the face-frame pairs; index m / m+1 carry (h, b), (um, s2), (s1, sc).
+    // The x halves of P's pairs are dead (P's own x-face is done), so each pair is reused with the
+    // shuffled value written into its x half.
     F2 Ln[m + 2], Lt[m + 2], Lgnn[m + 1], Lgnt[m + 1];
 #pragma unroll
     for (int k = 0; k < m; ++k) {
-        Ln[k] = F2(__shfl_up_sync(F, C.s.n[k].x(), 1), P.s.n[k].y());
-        Lt[k] = F2(__shfl_up_sync(F, C.s.t[k].x(), 1), P.s.t[k].y());
-        Lgnn[k] = F2(__shfl_up_sync(F, C.s.gnn[k].x(), 1), P.s.gnn[k].y());
-        Lgnt[k] = F2(__shfl_up_sync(F, C.s.gnt[k].x(), 1), P.s.gnt[k].y());
+        Ln[k] = P.s.n[k];
+        Ln[k].v.x = __shfl_up_sync(F, C.s.n[k].x(), 1);
+        Lt[k] = P.s.t[k];
+        Lt[k].v.x = __shfl_up_sync(F, C.s.t[k].x(), 1);
+        Lgnn[k] = P.s.gnn[k];
+        Lgnn[k].v.x = __shfl_up_sync(F, C.s.gnn[k].x(), 1);
+        Lgnt[k] = P.s.gnt[k];
+        Lgnt[k].v.x = __shfl_up_sync(F, C.s.gnt[k].x(), 1);
     }
     Ln[m] = F2(__shfl_up_sync(F, C.s.h, 1), P.s.h);      // depth
     Lt[m] = F2(__shfl_up_sync(F, C.s.b, 1), P.s.b);      // bed
@@ -349,7 +360,7 @@ __device__ __forceinline__ void row_body(const StageArgs<float> &a, const RowCtx
     F2 pr[1 + 2 * m], mi[1 + 2 * m];
     face2<N>(Ln, Lt, Lgnn, Lgnt, C.s, g, hdry, F2(dt * a.inv_dx, dt * a.inv_dy), pr, mi);
     // ---- scatter: x-face (.x) frame rows (alpha, beta); y-face (.y) frame rows (beta, alpha) ----
-    const bool yrow = r > r0 - 1;
+    const bool yrow = STEADY || r > r0 - 1;
     if (xrow) {
         float tl[nv];
         C.acc[0] += pr[0].x();
@@ -417,10 +428,9 @@ __device__ __forceinline__ void row_body(const StageArgs<float> &a, const RowCtx
                 const float so = c.owned ? s : 0.0f;
                 smax = (so > smax || so != so) ? so : smax;
             }
-            if (c.owned) {
-                const unsigned o = (unsigned)((r - 1) * c.nx + c.col);
+            if (c.owned) {  // (fin: orow is row r - 1; an owned lane's column is its source column)
 #pragma unroll
-                for (int v = 0; v < nv; ++v) a.out[o + (unsigned)(v * c.ld)] = y[v];
+                for (int v = 0; v < nv; ++v) orow[(unsigned)(v * c.ld)] = y[v];
             }
         }
     }
@@ -463,10 +473,19 @@ __device__ __forceinline__ void march_strip(const StageArgs<float> &a, int strip
     zero_state<N>(B);
     float nxt[nv + 1];
     load_row<N, STAGE>(a, c, r0 - 1, nxt);
-    for (int r = r0 - 1; r <= r1; r += 2) {
-        row_body<N, STAGE, IMP>(a, c, r, r0, r1, dt, nxt, B, A, smax, flag);
-        if (r + 1 <= r1) row_body<N, STAGE, IMP>(a, c, r + 1, r0, r1, dt, nxt, A, B, smax, flag);
+    // rows r0 - 1 and r0 with the general flags, then pairs of rows strictly inside the segment
+    // without any test (one straight block per pair, so consecutive rows' independent work can
+    // overlap), then the last one or two rows with the general flags again.  Row r uses A as its
+    // current state when r - r0 is odd.
+    int r = r0 - 1;
+    row_body<N, STAGE, IMP>(a, c, r, r0, r1, dt, nxt, B, A, smax, flag);
+    row_body<N, STAGE, IMP>(a, c, r + 1, r0, r1, dt, nxt, A, B, smax, flag);
+    for (r = r0 + 1; r + 1 < r1; r += 2) {
+        row_body<N, STAGE, IMP, true>(a, c, r, r0, r1, dt, nxt, B, A, smax, flag);
+        row_body<N, STAGE, IMP, true>(a, c, r + 1, r0, r1, dt, nxt, A, B, smax, flag);
     }
+    if (r <= r1) row_body<N, STAGE, IMP>(a, c, r, r0, r1, dt, nxt, B, A, smax, flag);
+    if (r + 1 <= r1) row_body<N, STAGE, IMP>(a, c, r + 1, r0, r1, dt, nxt, A, B, smax, flag);
 }
 
 }  // namespace zoomy

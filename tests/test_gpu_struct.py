@@ -278,24 +278,36 @@ def test_full_size_bench_state(Z, oracle):
     assert np.abs(got[1:] - ref64[1:]).max() <= 1e-6
 
 
-def test_decomposition_does_not_change_results(Z):
-    """Every cell is updated by one lane with the same arithmetic whatever the segment height, so the
-    result is bitwise independent of the launch configuration."""
+@pytest.mark.parametrize("level", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("case", ["slip_bathymetry", "manning_dry"])
+def test_decomposition_does_not_change_results(Z, level, case):
+    """Every cell is updated by one lane with the same arithmetic whatever the segment height (and
+    whether its row is a segment's first, last or an inner row), so the result, the CFL steps
+    included, is bitwise independent of the launch configuration: every level, walls on two sides and
+    transmissive ones on the others, over bathymetry and across Manning dry fronts."""
     import torch
 
-    nx, ny, level = 301, 203, 2
-    Q0 = inputs.random_moments_2d(nx, ny, level, seed=21)
-    _, bed = inputs.gaussian_bump_2d(nx, ny, level, seed=22)
+    nx, ny = 301, 203
+    if case == "manning_dry":
+        X, Y = inputs.centers_2d(nx, ny)
+        Q0 = np.zeros((inputs.nvars(level, 2), nx * ny))
+        Q0[0] = np.where((X - 0.4) ** 2 + (Y - 0.55) ** 2 < 0.05, 1.2, 0.0).reshape(-1)
+        bed, fr = None, Z.friction(2, manning_n=0.03)
+    else:
+        Q0 = inputs.random_moments_2d(nx, ny, level, seed=21 + level)
+        _, bed = inputs.gaussian_bump_2d(nx, ny, level, seed=22 + level)
+        fr = Z.friction(1, C=0.1, nu=0.01)
     outs = []
-    for tune in [(8, 1), (64, 1), (203, 1), (17, 4)]:
-        ctx = Z.Context(Z.mesh_2d(nx, ny, bathymetry=bed), level, Z.friction(1, C=0.1, nu=0.01), dtype=0)
+    for tune in [(8, 1), (64, 1), (203, 1), (17, 4), (5, 1)]:
+        ctx = Z.Context(Z.mesh_2d(nx, ny, bc=(1, 0, 0, 1), bathymetry=bed), level, fr, dtype=0)
         ctx.tune(*tune)
         Q = to_device(Q0, 0)
-        ctx.step(Q, nsteps=5, dt=0.0)
-        outs.append(Q.cpu())
+        t = ctx.step(Q, nsteps=5, dt=0.0)
+        outs.append((Q.cpu(), t))
         ctx.close()
-    for o in outs[1:]:
-        assert torch.equal(o, outs[0])
+    for o, t in outs[1:]:
+        assert torch.equal(o, outs[0][0]), (o - outs[0][0]).abs().max().item()
+        assert t == outs[0][1]
 
 
 def test_autotune_picks_a_valid_configuration(Z, tmp_path):
