@@ -106,7 +106,7 @@ def _declare(L):
     L.or_closure_eval.argtypes = [vp, _dp, _dp]
     L.or_closure_max_wavespeed.argtypes = [vp, vp, vp, _dp]
     L.or_closure_max_wavespeed.restype = C.c_double
-    L.or_step_closure.argtypes = [vp, vp, vp, _dp, vp, C.c_double, C.c_double, C.c_int, C.c_int,
+    L.or_step_closure.argtypes = [vp, vp, vp, _dp, vp, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int,
                                   C.POINTER(C.c_double)]
 
 
@@ -307,13 +307,14 @@ class Closure:
         return out
 
 
-def step_closure(model4, closure, mesh, Q1, nsteps, dt=0.0, cfl=0.45, bed=None, store_f32=False):
-    """nsteps SSP-RK2 steps of the closure model (level-1 state [5, nc], level-4 model)."""
+def step_closure(model4, closure, mesh, Q1, nsteps, dt=0.0, cfl=0.45, bed=None, store_f32=False, schedule=0):
+    """nsteps SSP-RK2 steps of the closure model (level-1 state [5, nc], level-4 model); schedule 0
+    evaluates the network on every stage input, 1 once per step on Q^n (held for both stages)."""
     Q = np.array(Q1, dtype=np.float64, order="C")
     b, bp = _bed_ptr(bed)
     t = C.c_double(0.0)
     rc = lib().or_step_closure(model4._p, closure._p, mesh._p, Q, bp, dt, cfl, nsteps, 1 if store_f32 else 0,
-                               C.byref(t))
+                               int(schedule), C.byref(t))
     if rc != 0:
         raise ValueError("closure step needs a 2D level-4 model")
     return Q, t.value

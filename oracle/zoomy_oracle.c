@@ -987,6 +987,9 @@ void or_lift3d(const or_model *md, const or_mesh *me, const double *Q, const dou
  * on the closed states, projected on the level-1 rows; the Newtonian source sums over all five
  * moments; the bottom stress is implicit in the two prognostic moments with the closed moments
  * frozen at the stage input; the CFL speed is the level-4 bound on the closed state.
+ * Schedule (reading R21): the network is evaluated on every stage input (schedule 0), or once per
+ * step on Q^n with its predicted velocity moments held for both stages (schedule 1): a stage input X
+ * then closes with alpha_hat(Q^n), cut to zero where X is dry, and its own depth.
  * GELU: tanh form.  bf16 != 0 rounds each layer input to BF16 (nearest, ties to even) like the
  * tensor-core inference kernel; all arithmetic is FP64.
  */
@@ -1057,10 +1060,9 @@ void or_closure_eval(const or_closure *c, const double *feat, double *out)
     }
 }
 
-/* The closed level-4 state of a level-1 state q1 (variables h, hA0, hB0, hA1, hB1); lambda is the
- * slip feature.  Returns the closed velocity moments in alpha_hat / beta_hat (k = 2..4). */
-static void closure_embed(const or_model *m4, const or_closure *c, const double *q1, double lambda, double *q4,
-                          double *ahat, double *bhat)
+/* The predicted velocity moments (alpha_2..4, beta_2..4) of a level-1 state q1 (variables h, hA0,
+ * hB0, hA1, hB1); lambda is the slip feature. */
+static void closure_predict(const or_model *m4, const or_closure *c, const double *q1, double lambda, double *out)
 {
     double h = q1[0];
     double u = 0.0, v = 0.0, a1 = 0.0, b1 = 0.0;
@@ -1070,8 +1072,16 @@ static void closure_embed(const or_model *m4, const or_closure *c, const double 
         a1 = q1[3] / h;
         b1 = q1[4] / h;
     }
-    double feat[6] = {h, u, v, a1, b1, lambda}, out[6];
+    double feat[6] = {h, u, v, a1, b1, lambda};
     or_closure_eval(c, feat, out);
+}
+
+/* The closed level-4 state of q1 with predicted velocity moments pred (zero where q1 is dry).
+ * Returns the closed moments in alpha_hat / beta_hat (k = 2..4). */
+static void closure_close(const or_model *m4, const double *q1, const double *pred, double *q4, double *ahat,
+                          double *bhat)
+{
+    double h = q1[0];
     for (int v2 = 0; v2 < m4->nv; ++v2) q4[v2] = 0.0;
     q4[0] = h;
     q4[ia(m4, 0)] = q1[1];
@@ -1079,16 +1089,25 @@ static void closure_embed(const or_model *m4, const or_closure *c, const double 
     q4[ia(m4, 1)] = q1[3];
     q4[ib(m4, 1)] = q1[4];
     for (int k = 2; k <= 4; ++k) {
-        ahat[k] = h > m4->h_dry ? out[k - 2] : 0.0;
-        bhat[k] = h > m4->h_dry ? out[k + 1] : 0.0;
+        ahat[k] = h > m4->h_dry ? pred[k - 2] : 0.0;
+        bhat[k] = h > m4->h_dry ? pred[k + 1] : 0.0;
         q4[ia(m4, k)] = h * ahat[k];
         q4[ib(m4, k)] = h * bhat[k];
     }
 }
 
+static void closure_embed(const or_model *m4, const or_closure *c, const double *q1, double lambda, double *q4,
+                          double *ahat, double *bhat)
+{
+    double out[6];
+    closure_predict(m4, c, q1, lambda, out);
+    closure_close(m4, q1, out, q4, ahat, bhat);
+}
+
 /* One closure stage Y = R(X + dt L(X)) on the level-1 state X [5][nc]. */
+/* pred: the predicted moments [nc][6] to close X with (schedule 1), or NULL to predict from X. */
 static void closure_stage(const or_model *m4, const or_closure *cl, const or_mesh *me, const double *X,
-                          const double *bed, double dt, double *Y)
+                          const double *bed, double dt, const double *pred, double *Y)
 {
     int64_t nc = me->nc;
     double *X4 = (double *)malloc(sizeof(double) * (size_t)m4->nv * nc);
@@ -1096,7 +1115,10 @@ static void closure_stage(const or_model *m4, const or_closure *cl, const or_mes
     for (int64_t i = 0; i < nc; ++i) {
         double q1[5], q4[OR_MAXV], ah[5], bh[5];
         for (int v = 0; v < 5; ++v) q1[v] = X[(int64_t)v * nc + i];
-        closure_embed(m4, cl, q1, m4->C, q4, ah, bh);
+        if (pred)
+            closure_close(m4, q1, pred + 6 * i, q4, ah, bh);
+        else
+            closure_embed(m4, cl, q1, m4->C, q4, ah, bh);
         for (int v = 0; v < m4->nv; ++v) X4[(int64_t)v * nc + i] = q4[v];
         sig[2 * i] = ah[2] + ah[3] + ah[4];
         sig[2 * i + 1] = bh[2] + bh[3] + bh[4];
@@ -1169,26 +1191,36 @@ double or_closure_max_wavespeed(const or_model *m4, const or_closure *cl, const 
 }
 
 /* nsteps SSP-RK2 steps of the closure model on the level-1 state Q1 [5][nc]; m4 is the level-4 2D
- * model (its C is the slip coefficient and the lambda feature).  store_f32 as in or_step_ex. */
+ * model (its C is the slip coefficient and the lambda feature).  store_f32 as in or_step_ex;
+ * schedule as in the header of this section. */
 int or_step_closure(const or_model *m4, const or_closure *cl, const or_mesh *me, double *Q1, const double *bed,
-                    double dt_fixed, double cfl, int nsteps, int store_f32, double *t_out)
+                    double dt_fixed, double cfl, int nsteps, int store_f32, int schedule, double *t_out)
 {
-    if (m4->N != 4 || m4->dim != 2) return 1;
+    if (m4->N != 4 || m4->dim != 2 || schedule < 0 || schedule > 1) return 1;
     int64_t n = 5 * me->nc;
     double *A = (double *)malloc(sizeof(double) * n);
     double *B = (double *)malloc(sizeof(double) * n);
+    double *P = schedule == 1 ? (double *)malloc(sizeof(double) * 6 * me->nc) : NULL;
     double t = 0.0;
     for (int s = 0; s < nsteps; ++s) {
         double dt = dt_fixed > 0.0 ? dt_fixed : cfl * or_min_delta(me) / or_closure_max_wavespeed(m4, cl, me, Q1);
-        closure_stage(m4, cl, me, Q1, bed, dt, A);
+        if (P) {
+            for (int64_t i = 0; i < me->nc; ++i) {
+                double q1[5];
+                for (int v = 0; v < 5; ++v) q1[v] = Q1[(int64_t)v * me->nc + i];
+                closure_predict(m4, cl, q1, m4->C, P + 6 * i);
+            }
+        }
+        closure_stage(m4, cl, me, Q1, bed, dt, P, A);
         if (store_f32) round_to_float(A, n);
-        closure_stage(m4, cl, me, A, bed, dt, B);
+        closure_stage(m4, cl, me, A, bed, dt, P, B);
         for (int64_t k = 0; k < n; ++k) Q1[k] = 0.5 * (Q1[k] + B[k]);
         if (store_f32) round_to_float(Q1, n);
         t += dt;
     }
     free(A);
     free(B);
+    free(P);
     if (t_out) *t_out = t;
     return 0;
 }

@@ -75,3 +75,65 @@ def test_constant_closure_uniform_flow_ode(oracle):
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert np.all(rates > 0.9), (errs, rates)
     assert errs[-1] < 2e-3 * np.abs(y0).max()
+
+
+def test_schedule_once_per_step_zero_closure_is_level1(oracle):
+    """Schedule 1 (network evaluated once per step on Q^n, held for both stages) with a zero network
+    is the plain level-1 scheme exactly, like schedule 0."""
+    nx, ny = 30, 22
+    Q1 = inputs.random_moments_2d(nx, ny, 1, seed=4, vel=0.25)
+    _, bed = inputs.gaussian_bump_2d(nx, ny, 1, seed=5)
+    mesh = oracle.Mesh.rect(nx, ny, 0, 1, 0, 1, bc=(1, 0, 1, 1))
+    m1 = oracle.Model(1, 2, g=G, friction=1, C=0.1, nu=0.01)
+    m4 = oracle.Model(4, 2, g=G, friction=1, C=0.1, nu=0.01)
+    R1, t1 = oracle.step(m1, mesh, Q1, 15, bed=bed)
+    Rc, tc = oracle.step_closure(m4, zero_closure(oracle), mesh, Q1, 15, bed=bed, schedule=1)
+    np.testing.assert_allclose(Rc, R1, rtol=1e-13, atol=1e-15)
+    assert tc == pytest.approx(t1, rel=1e-14)
+
+
+@pytest.mark.parametrize("fric", [(1, 0.2, 0.01, 0.0), (2, 0.0, 0.0, 0.03)])
+def test_schedule_once_per_step_constant_network_equals_every_stage(oracle, fric):
+    """A network whose output does not depend on its input predicts the same moments at Q^n and at
+    Q1, so both schedules give bitwise the same states, across a dry front too: a stage input closes
+    with its own depth and its own dry cut, whichever state the prediction came from."""
+    nx, ny = 28, 24
+    X, Y = inputs.centers_2d(nx, ny)
+    Q = np.zeros((5, nx * ny))
+    Q[0] = np.where((X - 0.45) ** 2 + (Y - 0.5) ** 2 < 0.06, 1.2, 0.0).reshape(-1)
+    Q[1] = 0.1 * Q[0]
+    Q[3] = -0.05 * Q[0]
+    p = {k: np.zeros_like(v) for k, v in mlp.init_params(0).items()}
+    p["b3"] = np.array([0.04, -0.02, 0.01, -0.03, 0.015, 0.005])
+    cl = oracle.Closure(mlp.pack(p), np.ones(6), np.ones(6), bf16=True)
+    kind, C_, nu, mn = fric
+    m4 = oracle.Model(4, 2, g=G, friction=kind, C=C_, nu=nu, manning_n=mn)
+    mesh = oracle.Mesh.rect(nx, ny, 0, 1, 0, 1, bc=(1, 1, 1, 1))
+    R0, t0 = oracle.step_closure(m4, cl, mesh, Q, 12, schedule=0)
+    R1, t1 = oracle.step_closure(m4, cl, mesh, Q, 12, schedule=1)
+    assert np.array_equal(R0, R1)
+    assert t0 == t1
+
+
+def test_schedule_once_per_step_differs_at_first_order(oracle):
+    """With a network that depends on the state, holding the step's prediction over stage 2 changes
+    the result by O(dt) at a fixed end time (the prediction lags by one stage): the difference
+    between the schedules halves with dt, and it is not zero."""
+    nx, ny = 20, 16
+    Q = inputs.random_moments_2d(nx, ny, 1, seed=9, vel=0.3)
+    rng = np.random.default_rng(3)
+    p = mlp.init_params(11)
+    for k in p:
+        p[k] = p[k] + 0.3 * rng.normal(size=p[k].shape)
+    cl = oracle.Closure(mlp.pack(p), np.ones(6), np.full(6, 0.2), bf16=False)
+    m4 = oracle.Model(4, 2, g=G, friction=1, C=0.1, nu=0.01)
+    mesh = oracle.Mesh.rect(nx, ny, 0, 1, 0, 1, bc=(1, 1, 1, 1))
+    T = 0.02
+    diffs = []
+    for n in (10, 20, 40):
+        R0, _ = oracle.step_closure(m4, cl, mesh, Q, n, dt=T / n, schedule=0)
+        R1, _ = oracle.step_closure(m4, cl, mesh, Q, n, dt=T / n, schedule=1)
+        diffs.append(np.abs(R1 - R0).max())
+    assert diffs[-1] > 0.0
+    rates = np.log2(np.array(diffs[:-1]) / np.array(diffs[1:]))
+    assert np.all((rates > 0.8) & (rates < 1.3)), (diffs, rates)

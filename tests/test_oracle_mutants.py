@@ -44,9 +44,14 @@ MUTANTS = {
     "order2_interior_nc_dropped": ("            acc[r] += len * a;", "            (void)a;"),
     "order2_slopes_unlimited": ("minmod(wi[v] - wl[v], wr[v] - wi[v])", "0.5 * (wr[v] - wl[v])"),
     "order2_face_bed_not_reconstructed": ("*bf = bi + 0.5 * s * (sig[1] - sig[0]);", "*bf = bi;"),
+    "closure_schedule_ignored_in_stage2": ("closure_stage(m4, cl, me, A, bed, dt, P, B);",
+                                           "closure_stage(m4, cl, me, A, bed, dt, NULL, B);"),
+    "closure_schedule1_drops_alpha2": ("closure_close(m4, q1, pred + 6 * i, q4, ah, bh);",
+                                            "closure_close(m4, q1, pred + 6 * i, q4, ah, bh), q4[ia(m4, 2)] = 0.0;"),
 }
 
 FIRST_PIN = {"tri_": "tests/test_oracle_triangles.py", "lift_": "tests/test_oracle_lift.py",
+             "closure_": "tests/test_oracle_closure.py",
              "implicit_": "tests/test_oracle_source.py", "order2_": "tests/test_oracle_order2.py"}
 PIN_TESTS = ["tests/test_oracle_basis.py", "tests/test_oracle_model.py", "tests/test_oracle_scheme.py",
              "tests/test_oracle_triangles.py", "tests/test_oracle_lift.py", "tests/test_oracle_source.py",
