@@ -207,16 +207,22 @@ def run_ours(args, rank, world, local_rank):
     with ClockSampler(local_rank) as clk:
         barrier()
         torch.cuda.synchronize()
-        zoomy.zoomy_profile_enable(ctx.ctx, True)
         e0.record(stream)
         ctx.step(Q, nsteps=args.steps, dt=0.0, sync=False)
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
     t_sim = zoomy.zoomy_sync(ctx.ctx)  # raises on a device-detected error
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    # per-kernel launch durations: the same steps again with CUDA events around every stage launch on
+    # the library's stream (an event between two launches ends their programmatic overlap, so the
+    # timed region above runs without them)
+    nprof = min(args.steps, 500)
+    zoomy.zoomy_profile_enable(ctx.ctx, True)
+    ctx.step(Q, nsteps=nprof, dt=0.0, sync=False)
+    zoomy.zoomy_sync(ctx.ctx)
     launches, kms = zoomy.zoomy_profile_read(ctx.ctx)
     zoomy.zoomy_profile_enable(ctx.ctx, False)
-    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
 
     # end-to-end through the host-buffer entry point: H2D of the state, one step, D2H of the result
     e2e_s = float("nan")
@@ -270,9 +276,11 @@ def run_ours(args, rank, world, local_rank):
                      "avg_launch_ms": {"stage1": avg1, "stage2": avg2}},
         "e2e": None if args.no_e2e else {"value": job_throughput(nc, 1, e2e_s, world), "unit": "cell-updates/s",
                                          "h2d_bytes_per_step": 4 * NV * nc, "d2h_bytes_per_step": 4 * NV * nc},
-        "gpu_launches": int(launches[0] + launches[1] + 1),
+        "gpu_launches": int(2 * args.steps + 1),
         "clocks": clk.summary(),
     }
+    line["roofline"]["launch_timing"] = (f"CUDA events around each stage launch, {nprof} steps right after the "
+                                         "timed region (same state, same launch configuration)")
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     return line
@@ -384,10 +392,10 @@ def run_closure_kernels(args):
     params = closure.init_params(0)
     ins = np.array([1.0, 4.0, 4.0, 50.0, 50.0, 4.0])
     outs = np.full(6, 1e-3)
-    r = closure.Run(side, 1, float(lam[0]), int(seeds[0]), closure=(params, ins, outs))
+    r = closure.Run(side, 1, float(lam[0]), int(seeds[0]), closure=(params, ins, outs),
+                    schedule=args.closure_schedule)
     zoomy.zoomy_closure_engine(r.ctx.ctx, args.closure_engine)
     r.ctx.step(r.Q, nsteps=args.warmup, dt=0.0)
-    zoomy.zoomy_profile_enable(r.ctx.ctx, True)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -396,17 +404,24 @@ def run_closure_kernels(args):
     e1.record(stream)
     torch.cuda.synchronize()
     zoomy.zoomy_sync(r.ctx.ctx)
-    launches, kms = zoomy.zoomy_profile_read(r.ctx.ctx)
     ms = e0.elapsed_time(e1)
+    # per-kernel durations in a second pass with events around every launch (they end the
+    # programmatic overlap of consecutive launches, so the timed pass runs without them)
+    zoomy.zoomy_profile_enable(r.ctx.ctx, True)
+    r.ctx.step(r.Q, nsteps=args.steps, dt=0.0, sync=False)
+    zoomy.zoomy_sync(r.ctx.ctx)
+    launches, kms = zoomy.zoomy_profile_read(r.ctx.ctx)
     r.close()
     flop_eval = 2 * (6 * 64 + 64 * 64 + 64 * 6)
     avg = [kms[i] / max(launches[i], 1) for i in range(3)]
     return {"metric": "closed level-1 step time", "value": ms / args.steps, "unit": "ms/step", "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": False,
             "config": {"workload": f"learned-closure step kernels, {side}x{side}, untrained network",
-                       "engine": ["tcgen05", "mma.sync"][args.closure_engine]},
+                       "engine": ["tcgen05", "mma.sync"][args.closure_engine],
+                       "schedule": ["every stage", "once per step"][args.closure_schedule]},
             "avg_launch_ms": {"stage1": avg[0], "stage2": avg[1], "predict": avg[2]},
-            "predict_tflops": flop_eval * side * side / (avg[2] * 1e-3) / 1e12, "gpu_launches": int(sum(launches))}
+            "predict_tflops": flop_eval * side * side / (avg[2] * 1e-3) / 1e12, "gpu_launches": int(sum(launches)),
+            "launch_timing": "per-kernel averages from a second pass with CUDA events around every launch"}
 
 
 def run_closure(args):
@@ -438,20 +453,25 @@ def run_closure(args):
     lam, seed = float(lam[0]), int(seeds[0])
     res = {}
     with ClockSampler(0) as clk:
-        for name, lv, cl in (("level4", 4, None), ("closure", 1, (params, ins, outs)), ("level1", 1, None)):
-            r = closure.Run(side, lv, lam, seed, closure=cl)
+        for name, lv, cl, sched in (("level4", 4, None, 0), ("closure", 1, (params, ins, outs), 1),
+                                    ("closure_every_stage", 1, (params, ins, outs), 0), ("level1", 1, None, 0)):
+            r = closure.Run(side, lv, lam, seed, closure=cl, schedule=sched)
             if cl is None:
                 r.ctx.autotune(r.Q)
             r.ctx.step(r.Q, nsteps=3, dt=1e-6)  # warm-up (module load, first launches)
             r.Q.copy_(closure.Run.initial(side, lv, seed))
-            zoomy.zoomy_profile_enable(r.ctx.ctx, True)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             nsteps = r.run_to(T)
             torch.cuda.synchronize()
             wall = time.perf_counter() - t0
+            state = r.mean_state()
+            # per-kernel durations: 100 more steps with CUDA events around every launch (not timed above:
+            # the events end the programmatic overlap of consecutive launches)
+            zoomy.zoomy_profile_enable(r.ctx.ctx, True)
+            r.ctx.step(r.Q, nsteps=100, dt=1e-5)
             launches, kms = zoomy.zoomy_profile_read(r.ctx.ctx)
-            res[name] = {"time_s": wall, "steps": nsteps, "state": r.mean_state(),
+            res[name] = {"time_s": wall, "steps": nsteps, "state": state,
                          "kernel_ms": [kms[i] / max(launches[i], 1) for i in range(3)],
                          "launches": int(sum(launches))}
             r.close()
@@ -476,9 +496,13 @@ def run_closure(args):
                                     "data_s": t_data, "train_s": t_train, "loss": hist[-1][1]}},
             "level4": {"time_s": l4["time_s"], "steps": l4["steps"], "ms_per_step": 1e3 * l4["time_s"] / l4["steps"]},
             "level1": {"time_s": res["level1"]["time_s"], "steps": res["level1"]["steps"]},
+            "closure_every_stage": {"time_s": res["closure_every_stage"]["time_s"],
+                                    "steps": res["closure_every_stage"]["steps"],
+                                    "speedup_vs_level4": l4["time_s"] / res["closure_every_stage"]["time_s"]},
             "speedup_vs_level4": l4["time_s"] / cl_["time_s"],
-            "rel_l1_vs_level4": {"closure": l1(cl_["state"]), "level1": l1(res["level1"]["state"]),
-                                 "vars": ["h", "h u_m", "h v_m"]},
+            "closure_schedule": "once per step (network on Q^n, held for both stages)",
+            "rel_l1_vs_level4": {"closure": l1(cl_["state"]), "closure_every_stage": l1(res["closure_every_stage"]["state"]),
+                                 "level1": l1(res["level1"]["state"]), "vars": ["h", "h u_m", "h v_m"]},
             "roofline": {"bound": "tensor", "kernel": "k_closure_predict", "achieved": ach, "peak": pk[0],
                          "peak_kind": pk[1], "unit": "TFLOP/s", "frac": ach / pk[0], "traffic": None,
                          "algorithmic_flop_per_launch": flop_eval * cells,
@@ -702,6 +726,8 @@ def main():
                     help="lattice side of the triangle workload (1415: ~4M triangles; smaller for profiling runs)")
     ap.add_argument("--closure-train-side", type=int, default=128, help="grid side of the training runs")
     ap.add_argument("--closure-engine", type=int, default=0, help="closure network engine: 0 tcgen05, 1 mma.sync")
+    ap.add_argument("--closure-schedule", type=int, default=1, choices=[0, 1],
+                    help="closure-kernels: network on every stage input (0) or once per step (1)")
     ap.add_argument("--rows-per-warp", type=int, default=0,
                     help="fixed structured-kernel segment height instead of the autotuner (profiling runs)")
     args = ap.parse_args()

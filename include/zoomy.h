@@ -181,6 +181,16 @@ zoomy_status zoomy_sync(zoomy_ctx *ctx, double *t_total);
  * eigenstructure of A . n) used for the CFL step. */
 zoomy_status zoomy_max_wavespeed(zoomy_ctx *ctx, const void *Q, int64_t ld, double *out);
 
+/* Advance Q (device) to the time t_end from now with CFL steps and land on t_end exactly: chunks of
+ * at most `chunk` steps, each sized from the current maximum wave speed (zoomy_max_wavespeed, one
+ * synchronisation per chunk) to stay below t_end, then one or two fixed steps of equal length once
+ * fewer than about 1.25 CFL steps remain (neither longer than the CFL step).  The paper's solver runs
+ * to a final time the same way (Sec. 3.1: adaptive step, end time).  *t_out: time advanced (t_end
+ * up to rounding), *steps_out: steps taken (both may be NULL).  Errors as zoomy_step; ZOOMY_EINVAL
+ * for t_end < 0 or chunk < 1. */
+zoomy_status zoomy_advance(zoomy_ctx *ctx, void *Q, int64_t ld, double t_end, int32_t chunk, double *t_out,
+                           int64_t *steps_out);
+
 /* sum_i |Omega_i| h_i accumulated in FP64 in a fixed order (device Q, synchronises). */
 zoomy_status zoomy_mass(zoomy_ctx *ctx, const void *Q, int64_t ld, double *out);
 
@@ -228,6 +238,13 @@ zoomy_status zoomy_closure_eval(zoomy_ctx *ctx, const float *feat, float *out, i
  * the FP32 accumulation.  EINVAL for other values. */
 zoomy_status zoomy_closure_engine(zoomy_ctx *ctx, int32_t engine);
 
+/* When the closure network is evaluated (the paper's material closure of Sec. 1 / Sec. 3.4 is
+ * exchangeable and leaves this open; reading R21): schedule 0 (default) on every SSP-RK2 stage
+ * input; schedule 1 once per step on Q^n, its predicted velocity moments held for both stages (each
+ * stage input closes with its own depth and dry cut).  Schedule 1 halves the network evaluations;
+ * the two differ by O(dt) at a fixed end time.  EINVAL for other values. */
+zoomy_status zoomy_closure_schedule(zoomy_ctx *ctx, int32_t schedule);
+
 /* ---- Training the closure MLP ------------------------------------------------------------------
  * Full-batch (or caller-sliced mini-batch) training of the closure network above by hand-written
  * kernels: forward and backward passes one thread per sample (FP32, weights in shared memory), the
@@ -260,6 +277,18 @@ zoomy_status zoomy_mlp_train_step(zoomy_mlp *mlp, const float *X, const float *T
 zoomy_status zoomy_closure_samples(const float *Q, int64_t ld, int32_t level, const int64_t *cells, int64_t n,
                                    double lambda, double h_dry, const float *in_scale, const float *out_scale,
                                    float *X, float *T, void *stream);
+
+/* Scale factors of a training set X, T (device, [n][6] each; the closure network's features and
+ * targets): in_scale[j] = 1 / max_s |X[s][j]|, out_scale[j] = max_s |T[s][j]| (floored at 1e-12),
+ * into host arrays [6].  Synchronises `stream`.  The paper trains no network; this serves the
+ * learned closure (zoomy_closure_set). */
+zoomy_status zoomy_sample_scales(const float *X, const float *T, int64_t n, float *in_scale, float *out_scale,
+                                 void *stream);
+
+/* In place on the device: X[s][j] *= in_scale[j], T[s][j] /= out_scale[j] for s < n (in_scale,
+ * out_scale: device [6]).  Queued on `stream`. */
+zoomy_status zoomy_sample_scale(float *X, float *T, int64_t n, const float *in_scale, const float *out_scale,
+                                void *stream);
 
 /* ---- Lifting to three-dimensional fields ---------------------------------------------------------
  * The paper's interpolate_3d postprocessing (Sec. "Postprocessing"): from the state Q (device,

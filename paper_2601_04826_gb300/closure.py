@@ -69,26 +69,24 @@ def generate_samples(nmembers=32, side=64, level=4, T=2.0, snapshots=8, seed=0, 
 
 
 def scales(F, Y):
-    """in_scale = 1 / max|feature|, out_scale = max|target| (per column, from the data)."""
-    import torch
-
-    fin = torch.amax(torch.abs(F), dim=0).double().cpu().numpy()
-    fout = torch.amax(torch.abs(Y), dim=0).double().cpu().numpy()
-    return 1.0 / np.maximum(fin, 1e-12), np.maximum(fout, 1e-12)
+    """in_scale = 1 / max|feature|, out_scale = max|target| per column (zoomy_sample_scales)."""
+    ins, outs = zoomy.zoomy_sample_scales(F, Y, F.shape[0])
+    return np.asarray(ins, dtype=np.float64), np.asarray(outs, dtype=np.float64)
 
 
 def fit(F, Y, in_scale, out_scale, steps=3000, batch=16384, lr=3e-3, lr_final=1e-3, seed=0, params=None):
     """Train on mini-batches of a seeded permutation of the samples (deterministic).  Returns
-    (params float32 [4998], list of (step, loss) every 500 steps)."""
+    (params float32 [4998], list of (step, loss) every 500 steps).  F and Y are left unchanged."""
     import torch
 
-    X = F * torch.tensor(in_scale, dtype=torch.float32, device=F.device)
-    T = Y / torch.tensor(out_scale, dtype=torch.float32, device=F.device)
+    ins = torch.tensor(in_scale, dtype=torch.float32, device=F.device)
+    outs = torch.tensor(out_scale, dtype=torch.float32, device=F.device)
     g = torch.Generator(device=F.device)
     g.manual_seed(seed)
-    perm = torch.randperm(X.shape[0], generator=g, device=F.device)
-    X = X[perm].contiguous()
-    T = T[perm].contiguous()
+    perm = torch.randperm(F.shape[0], generator=g, device=F.device)
+    X = F[perm].contiguous()  # a shuffled copy, scaled in place by the library
+    T = Y[perm].contiguous()
+    zoomy.zoomy_sample_scale(X, T, X.shape[0], ins, outs)
     n = X.shape[0]
     batch = min(batch, n)
     nb = n // batch
@@ -109,31 +107,18 @@ def fit(F, Y, in_scale, out_scale, steps=3000, batch=16384, lr=3e-3, lr_final=1e
 
 
 def advance_to(ctx, Q, T, chunk=256):
-    """Advance a context's state with CFL steps and land exactly on time T (the last one or two
-    steps take a fixed dt no larger than the CFL step).  Returns the number of steps taken."""
-    t, steps = 0.0, 0
-    while T - t > 1e-12 * T:
-        rem = T - t
-        smax = ctx.max_wavespeed(Q)
-        dt_est = ctx.cfl * ctx.min_delta / smax
-        n = min(chunk, int(0.8 * rem / dt_est) - 1)
-        if n >= 1:
-            t += ctx.step(Q, nsteps=n, dt=0.0)
-            steps += n
-        else:
-            k = 1 if rem <= dt_est else 2
-            for _ in range(k):
-                t += ctx.step(Q, nsteps=1, dt=rem / k)
-            steps += k
-            break
+    """Advance a context's state with CFL steps and land exactly on time T (zoomy_advance).  Returns
+    the number of steps taken."""
+    _, steps = ctx.advance(Q, T, chunk)
     return steps
 
 
 class Run:
     """One structured 2D FP32 run of a bump member: level `level`, or level 1 closed by a trained
-    network (closure=(params, in_scale, out_scale))."""
+    network (closure=(params, in_scale, out_scale)) evaluated on the schedule given (0: every stage
+    input, 1: once per step)."""
 
-    def __init__(self, side, level, lam, member_seed, nu=0.01, cfl=0.45, h_dry=1e-6, closure=None):
+    def __init__(self, side, level, lam, member_seed, nu=0.01, cfl=0.45, h_dry=1e-6, closure=None, schedule=0):
         lv = 1 if closure is not None else level
         self.ctx = zoomy.Context(zoomy.mesh_2d(side, side, bc=(1, 1, 1, 1)), lv,
                                  zoomy.friction(zoomy.FRICTION_SLIP_NEWTONIAN, C=lam, nu=nu), g=G, cfl=cfl,
@@ -142,6 +127,7 @@ class Run:
         if closure is not None:
             p, i, o = closure
             zoomy.zoomy_closure_set(self.ctx.ctx, p, i, o, lam)
+            zoomy.zoomy_closure_schedule(self.ctx.ctx, schedule)
         self.Q = self.initial(side, lv, member_seed)
 
     @staticmethod

@@ -13,6 +13,7 @@
 // batch of two m16 tiles of mma.sync.m16n8k16 BF16 operations; the accumulator fragments of layer 1
 // and 2 are re-packed in registers as the A operands of the next layer, and the weight fragments sit
 // pre-swizzled in shared memory.
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -20,6 +21,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include "closure_stage.cuh"
 #include "f32x2.cuh"
 #include "fv_common.cuh"
 #include "tcgen05.cuh"
@@ -28,9 +30,6 @@
 
 namespace zoomy {
 
-constexpr int CL_M = 5;   // moments of the closed profile (level 4)
-constexpr int CL_NV = 5;  // prognostic variables (level 1, 2D)
-
 // weight fragments in the layout of the mma.sync B operand (per lane), then FP32 biases
 struct ClosureDev {
     uint32_t w1[8][32];     // layer 1: n-tile, lane -> b0 (rows 2t,2t+1 of the padded 16-row W1)
@@ -38,14 +37,6 @@ struct ClosureDev {
     uint2 w3[4][32];        // layer 3: k-chunk, lane -> (b0, b1) (outputs padded 6 -> 8)
     float b1[64], b2[64], b3[8];
     float in_scale[6], out_scale[6];
-};
-
-struct ClosureArgs {
-    StageArgs<float> s;
-    const ClosureDev *net;
-    float *pred;      // predicted closed moments of the stage input, SoA [6][pstride]
-    int64_t pstride;  // nx * ny
-    float lambda;
 };
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
@@ -77,6 +68,24 @@ __device__ __forceinline__ float gelu(float z)
     const float u = 0.7978845608028654f * z * fmaf(0.044715f, z * z, 1.0f);
     const float hz = 0.5f * z;
     return fmaf(hz, tanh_approx(u), hz);
+}
+
+// GELU of a pair in terms of h = z/2 without the SFU: GELU(z) = h + h tanh(h (2c + 8 * 0.044715 c
+// h^2)) = h + E(h^2), with E(s) approximated by s P(s), P of degree 6, fitted (least squares with
+// Lawson's reweighting towards the minimax error) on Chebyshev nodes of s in [0, 4]; for |h| > 2 the
+// tanh is 1 to 4e-5 and E = |h|.  Largest error against the tanh form: 2.1e-4 absolute, below the
+// error of tanh.approx.f32 there (|h| 2^-11) and of the BF16 rounding that follows.
+__device__ __forceinline__ F2 gelu_poly2(F2 h)
+{
+    const F2 s = h * h;
+    F2 p = fma2(F2(3.9228369132615626e-04f), s, F2(-6.8186875432729721e-03f));
+    p = fma2(p, s, F2(5.0590563565492630e-02f));
+    p = fma2(p, s, F2(-2.1221332252025604e-01f));
+    p = fma2(p, s, F2(5.6576108932495117e-01f));
+    p = fma2(p, s, F2(-1.0342786312103271e+00f));
+    p = fma2(p, s, F2(1.5909816026687622e+00f));
+    const F2 e = s * p;
+    return h + F2(s.x() > 4.0f ? fabsf(h.x()) : e.x(), s.y() > 4.0f ? fabsf(h.y()) : e.y());
 }
 
 // Warp-cooperative MLP of the 32 cells held by the lanes (one cell per lane).
@@ -158,170 +167,13 @@ __device__ __forceinline__ void mlp_warp(const ClosureDev *net, const float *fea
     __syncwarp();
 }
 
-// Closed cell record (scalar FP32).
-struct CRec {
-    float h, b;
-    float a[CL_M], c[CL_M];       // alpha_k, beta_k of the closed profile (zero where dry)
-    float um, s2, s1;
-    float gaa[2], gab[2], gbb[2];  // flux products of rows k = 0, 1
-    float sa, sb;                  // sum_{k>=2} alpha_k, beta_k (closed part, for the bottom stress)
-};
-
-__device__ __forceinline__ void make_crec(CRec &r, float h, float b, const float *q, const float *pred, bool xwall,
-                                          bool ywall, float hdry)
+// Wave speed of the closed profile of a cell: state x, predictions p (the level-4 bound R3).
+__device__ __forceinline__ float closed_speed(const float *x, const float *p, float g, float hdry)
 {
-    const bool wet = h > hdry;
-    const float ih = wet ? __frcp_rn(h) : 0.0f;
-    r.h = h;
-    r.b = b;
-    r.a[0] = q[1] * ih;
-    r.c[0] = q[2] * ih;
-    r.a[1] = q[3] * ih;
-    r.c[1] = q[4] * ih;
-#pragma unroll
-    for (int k = 2; k < CL_M; ++k) {
-        r.a[k] = wet ? pred[k - 2] : 0.0f;
-        r.c[k] = wet ? pred[k + 1] : 0.0f;
-    }
-#pragma unroll
-    for (int k = 0; k < CL_M; ++k) {
-        if (xwall) r.a[k] = -r.a[k];
-        if (ywall) r.c[k] = -r.c[k];
-    }
-    r.sa = r.a[2] + r.a[3] + r.a[4];
-    r.sb = r.c[2] + r.c[3] + r.c[4];
-    r.um = sqrtf(r.a[0] * r.a[0] + r.c[0] * r.c[0]);
-    float s2 = 0.f, s1 = 0.f;
-#pragma unroll
-    for (int k = 1; k < CL_M; ++k) {
-        const float q2 = r.a[k] * r.a[k] + r.c[k] * r.c[k];
-        s2 += q2;
-        if (k >= 2) s1 += sqrtf(q2);
-    }
-    r.s2 = s2;
-    r.s1 = s1;
-    static_for<0, 2>([&](auto kk) {
-        constexpr int k = decltype(kk)::value;
-        float saa = 0.f, sab = 0.f, sbb = 0.f;
-        static_for<0, CL_M>([&](auto ii) {
-            constexpr int i = decltype(ii)::value;
-            static_for<0, CL_M>([&](auto jj) {
-                constexpr int j = decltype(jj)::value;
-                constexpr double w = fluxA(i, j, k);
-                if constexpr (w != 0.0) {
-                    if constexpr (j >= i) {
-                        constexpr double w2 = (i == j) ? w : 2.0 * w;
-                        saa += float(w2) * r.a[i] * r.a[j];
-                        sbb += float(w2) * r.c[i] * r.c[j];
-                    }
-                    sab += float(w) * r.a[i] * r.c[j];
-                }
-            });
-        });
-        r.gaa[k] = saa;
-        r.gab[k] = sab;
-        r.gbb[k] = sbb;
-    });
-}
-
-// Face terms of the restricted model in a face frame (n, t): rows mass, n_0, n_1, t_0, t_1.
-// out: fc[5] (mass, n0, n1, t0, t1) and nc[5] (only n1, t1 are non-zero), pd on n0.
-template <bool YDIR>
-__device__ __forceinline__ void face_closure(const CRec &L, const CRec &R, float g, float hdry, float *fc, float &pd,
-                                             float *nc)
-{
-    const float *nL = YDIR ? L.c : L.a, *tL = YDIR ? L.a : L.c;
-    const float *nR = YDIR ? R.c : R.a, *tR = YDIR ? R.a : R.c;
-    const float *gnnL = YDIR ? L.gbb : L.gaa, *gnnR = YDIR ? R.gbb : R.gaa;
-    const float bf = fmaxf(L.b, R.b);
-    const HPair pl = hr_depth(L.h, L.b, bf), pr = hr_depth(R.h, R.b, bf);
-    const float hl = hp_val(pl), hr = hp_val(pr), dh = hp_diff(pr, pl);
-    const bool wl = hl > hdry, wr = hr > hdry;
-    const float sl = wl ? L.um + sqrtf(g * hl + L.s2) + L.s1 : sqrtf(g * hl);
-    const float sr = wr ? R.um + sqrtf(g * hr + R.s2) + R.s1 : sqrtf(g * hr);
-    const float hs = 0.5f * fmaxf(sl, sr);
-    const float el = wl ? hl : 0.0f, er = wr ? hr : 0.0f;
-    float dn[CL_M], dtv[2];
-#pragma unroll
-    for (int k = 0; k < CL_M; ++k) dn[k] = er * nR[k] - el * nL[k];
-    dtv[0] = er * tR[0] - el * tL[0];
-    dtv[1] = er * tR[1] - el * tL[1];
-    fc[0] = 0.5f * (el * nL[0] + er * nR[0]) - hs * dh;
-    fc[1] = 0.5f * (el * gnnL[0] + er * gnnR[0]) - hs * dn[0];
-    fc[2] = 0.5f * (el * gnnL[1] + er * gnnR[1]) - hs * dn[1];
-    fc[3] = 0.5f * (el * L.gab[0] + er * R.gab[0]) - hs * dtv[0];
-    fc[4] = 0.5f * (el * L.gab[1] + er * R.gab[1]) - hs * dtv[1];
-    pd = 0.25f * g * dh * (hr + hl);
-    // path-averaged closed profiles (3-point Gauss-Legendre, weights W0/W1 as in the structured kernels)
-    constexpr float sq15 = 0.38729833462074168852f;
-    const float sn[3] = {0.5f - sq15, 0.5f, 0.5f + sq15};
-    const float wq[3] = {5.0f / 18.0f, 8.0f / 18.0f, 5.0f / 18.0f};
-    float W0 = 0.f, W1 = 0.f;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        const float hq = fmaf(sn[q], dh, hl);
-        const float iw = hq > hdry ? wq[q] * __frcp_rn(hq) : 0.0f;
-        W0 += iw;
-        W1 = fmaf(sn[q], iw, W1);
-    }
-    float nb[CL_M], tb[CL_M];
-#pragma unroll
-    for (int k = 0; k < CL_M; ++k) {
-        nb[k] = el * nL[k] * W0 + dn[k] * W1;
-        tb[k] = el * tL[k] * W0 + (er * tR[k] - el * tL[k]) * W1;
-    }
-    float rn = 0.f, rt = 0.f;
-    static_for<1, CL_M>([&](auto ll) {
-        constexpr int l = decltype(ll)::value;
-        float en = 0.f, et = 0.f;
-        static_for<0, CL_M>([&](auto jj) {
-            constexpr int j = decltype(jj)::value;
-            constexpr double w = ncB(1, j, l);
-            if constexpr (w != 0.0) {
-                en += float(w) * nb[j];
-                et += float(w) * tb[j];
-            }
-        });
-        rn += en * dn[l];
-        rt += et * dn[l];
-    });
-    nc[0] = nc[1] = nc[3] = 0.0f;
-    nc[2] = 0.5f * rn;
-    nc[4] = 0.5f * rt;
-}
-
-__device__ __forceinline__ CRec shfl_up_crec(const CRec &r)
-{
-    constexpr unsigned F = 0xffffffffu;
-    CRec o;
-    o.h = __shfl_up_sync(F, r.h, 1);
-    o.b = __shfl_up_sync(F, r.b, 1);
-    o.um = __shfl_up_sync(F, r.um, 1);
-    o.s2 = __shfl_up_sync(F, r.s2, 1);
-    o.s1 = __shfl_up_sync(F, r.s1, 1);
-#pragma unroll
-    for (int k = 0; k < CL_M; ++k) {
-        o.a[k] = __shfl_up_sync(F, r.a[k], 1);
-        o.c[k] = __shfl_up_sync(F, r.c[k], 1);
-    }
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        o.gaa[k] = __shfl_up_sync(F, r.gaa[k], 1);
-        o.gab[k] = __shfl_up_sync(F, r.gab[k], 1);
-        o.gbb[k] = 0.0f;
-    }
-    o.sa = o.sb = 0.0f;
-    return o;
-}
-
-// frame row (mass, n0, n1, t0, t1) -> variable (h, hA0, hB0, hA1, hB1)
-template <bool YDIR>
-__device__ __forceinline__ int cl_var(int row)
-{
-    // x-face: n = alpha, t = beta;  y-face: n = beta, t = alpha
-    const int xmap[5] = {0, 1, 3, 2, 4};
-    const int ymap[5] = {0, 2, 4, 1, 3};
-    return YDIR ? ymap[row] : xmap[row];
+    SideC r;
+    float ih;
+    make_side_c(r, x, 0.0f, p, false, false, g, hdry, ih);
+    return r.sc;
 }
 
 __device__ __forceinline__ void features(const float *q, float lambda, float hdry, float *f)
@@ -336,11 +188,12 @@ __device__ __forceinline__ void features(const float *q, float lambda, float hdr
     f[5] = lambda;
 }
 
+// The FV stage of the closed model (closure_stage.cuh): one warp per CTA marches a 30-column strip.
 template <int STAGE>
-__global__ void __launch_bounds__(128) k_stage_closure(ClosureArgs ca)
+__global__ void __launch_bounds__(32) k_stage_closure(ClosureArgs ca)
 {
     const StageArgs<float> &a = ca.s;
-    constexpr unsigned F = 0xffffffffu;
+    pdl_enter();  // programmatic dependent launch: the prediction of this stage's input first
     if (*(volatile unsigned int *)&a.ctl->status) return;
     float dt;
     if (!step_dt(a, dt)) {
@@ -348,157 +201,8 @@ __global__ void __launch_bounds__(128) k_stage_closure(ClosureArgs ca)
         return;
     }
     if (STAGE == 1 && blockIdx.x == 0 && threadIdx.x == 0) step_bookkeeping(a, dt);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int wg = blockIdx.x * 4 + warp;
-    const int strip = wg % a.nstrips, seg = wg / a.nstrips;
-    if (seg >= a.nsegs) return;
-    const int col = strip * 30 - 1 + lane;
-    const bool owned = lane >= 1 && lane <= 30 && col < a.nx;
-    const int csrc = col < 0 ? 0 : (col >= a.nx ? a.nx - 1 : col);
-    const bool xwall = (col < 0 && a.bc[0] == 1) || (col >= a.nx && a.bc[1] == 1);
-    const int r0 = seg * a.H, r1 = min(r0 + a.H, a.ny);
-    const float g = a.g, hdry = a.hdry;
-
-    CRec prev, cur;
-    {
-        const float z[6] = {0, 0, 0, 0, 0, 0};
-        const float q0[5] = {0, 0, 0, 0, 0};
-        make_crec(prev, 0.0f, 0.0f, q0, z, false, false, hdry);
-    }
-    float xprev[CL_NV] = {0, 0, 0, 0, 0}, accp[CL_NV] = {0, 0, 0, 0, 0};
     unsigned flag = 0;
-    // the next row's state, bed and predictions are loaded one iteration ahead
-    float xn[CL_NV], bn, pn[6];
-    auto load_row = [&](int rr) {
-        const int rs = rr < 0 ? 0 : (rr >= a.ny ? a.ny - 1 : rr);
-        const int64_t idx = (int64_t)rs * a.nx + csrc;
-#pragma unroll
-        for (int v = 0; v < CL_NV; ++v) xn[v] = __ldg(a.X + v * a.ld + idx);
-        bn = __ldg(a.bed + idx);
-#pragma unroll
-        for (int j = 0; j < 6; ++j) pn[j] = __ldg(ca.pred + j * ca.pstride + idx);
-    };
-    load_row(r0 - 1);
-    for (int r = r0 - 1; r <= r1; ++r) {
-        const bool ywall = (r < 0 && a.bc[2] == 1) || (r >= a.ny && a.bc[3] == 1);
-        float x[CL_NV], pred[6];
-#pragma unroll
-        for (int v = 0; v < CL_NV; ++v) x[v] = xn[v];
-        const float bed = bn;
-        // closure of this row's cells (predicted from the unreflected state; ghosts reflect it)
-#pragma unroll
-        for (int j = 0; j < 6; ++j) pred[j] = pn[j];
-        if (r < r1) load_row(r + 1);
-        // Q^n of the row finished in this iteration (stage 2), requested before the face work
-        float qn[CL_NV];
-        if (STAGE == 2) {
-            const int64_t qidx = (int64_t)(r - 1 >= r0 ? r - 1 : r0) * a.nx + csrc;
-#pragma unroll
-            for (int v = 0; v < CL_NV; ++v) qn[v] = __ldg(a.Qn + v * a.ld + qidx);
-        }
-        float q[CL_NV];
-#pragma unroll
-        for (int v = 0; v < CL_NV; ++v) q[v] = x[v];
-        make_crec(cur, x[0], bed, q, pred, xwall, ywall, hdry);
-
-        float accc[CL_NV] = {0, 0, 0, 0, 0};
-        float fc[5], nc[5], pd;
-        const bool xrow = r >= r0 && r < r1;
-        if (xrow) {
-            const CRec left = shfl_up_crec(cur);
-            face_closure<false>(left, cur, g, hdry, fc, pd, nc);
-            float tl[CL_NV];
-#pragma unroll
-            for (int row = 0; row < 5; ++row) {
-                const int v = cl_var<false>(row);
-                const float pdr = row == 1 ? pd : 0.0f;
-                accc[v] += a.inv_dx * (fc[row] - pdr - nc[row]);
-                tl[v] = a.inv_dx * (fc[row] + pdr + nc[row]);
-            }
-#pragma unroll
-            for (int v = 0; v < CL_NV; ++v) accc[v] -= __shfl_down_sync(F, tl[v], 1);
-        }
-        if (r > r0 - 1) {
-            face_closure<true>(prev, cur, g, hdry, fc, pd, nc);
-#pragma unroll
-            for (int row = 0; row < 5; ++row) {
-                const int v = cl_var<true>(row);
-                const float pdr = row == 1 ? pd : 0.0f;
-                accp[v] -= a.inv_dy * (fc[row] + pdr + nc[row]);
-                accc[v] += a.inv_dy * (fc[row] - pdr - nc[row]);
-            }
-            const bool fin = r - 1 >= r0;
-            if (fin) {  // row r-1 is complete (all lanes compute; owners store)
-                // Newtonian bulk stress of the closed profile, rows k = 0, 1
-                const float f0 = prev.h > 0.0f ? a.nu_rho / prev.h : 0.0f;
-                float sa[2], sb[2];
-                static_for<0, 2>([&](auto kk) {
-                    constexpr int k = decltype(kk)::value;
-                    float xa = 0.f, xb = 0.f;
-                    static_for<0, CL_M>([&](auto ii) {
-                        constexpr int i = decltype(ii)::value;
-                        constexpr double w = visC(i, k);
-                        if constexpr (w != 0.0) {
-                            xa += float(w) * prev.a[i];
-                            xb += float(w) * prev.c[i];
-                        }
-                    });
-                    sa[k] = -f0 * xa;
-                    sb[k] = -f0 * xb;
-                });
-                float y[CL_NV];
-                y[0] = xprev[0] + dt * accp[0];
-                y[1] = xprev[1] + dt * accp[1] + dt * sa[0];
-                y[2] = xprev[2] + dt * accp[2] + dt * sb[0];
-                y[3] = xprev[3] + dt * accp[3] + dt * sa[1];
-                y[4] = xprev[4] + dt * accp[4] + dt * sb[1];
-                // bottom stress: implicit in (alpha_0, alpha_1), closed moments frozen at the stage input
-                const float h = y[0];
-                const bool wet = h > hdry;
-                const float ih = __frcp_rn(h);
-                const float sah = h * prev.sa, sbh = h * prev.sb;
-                float cc = 0.0f;
-                if (a.fric == 1) {
-                    cc = a.C_rho * ih;
-                } else if (a.fric == 2) {
-                    const float ub = (y[1] + y[3] + sah) * ih, vb = (y[2] + y[4] + sbh) * ih;
-                    cc = a.gn2 * sqrtf(ub * ub + vb * vb) * ih / cbrtf(h);
-                }
-                const float dc = dt * cc;
-                const float ra0 = y[1] - dc * sah, ra1 = y[3] - 3.0f * dc * sah;
-                const float rb0 = y[2] - dc * sbh, rb1 = y[4] - 3.0f * dc * sbh;
-                const float den = 1.0f + 4.0f * dc;
-                const float fa = dc * (ra0 + ra1) / den, fb = dc * (rb0 + rb1) / den;
-                y[1] = wet ? ra0 - fa : 0.0f;
-                y[3] = wet ? ra1 - 3.0f * fa : 0.0f;
-                y[2] = wet ? rb0 - fb : 0.0f;
-                y[4] = wet ? rb1 - 3.0f * fb : 0.0f;
-                const int64_t oidx = (int64_t)(r - 1) * a.nx + (owned ? col : csrc);
-                if (STAGE == 2) {
-#pragma unroll
-                    for (int v = 0; v < CL_NV; ++v) y[v] = 0.5f * (qn[v] + y[v]);
-                    // (the next step's prediction kernel takes the new state's wave speed)
-                    if (owned) {
-                        bool bad = false;
-#pragma unroll
-                        for (int v = 0; v < CL_NV; ++v) bad |= !(fabsf(y[v]) <= 3.0e38f);
-                        if (bad) flag |= DEV_NAN;
-                        if (y[0] < 0.0f) flag |= DEV_NEGDEPTH;
-                    }
-                }
-                if (owned) {
-#pragma unroll
-                    for (int v = 0; v < CL_NV; ++v) a.out[v * a.ld + oidx] = y[v];
-                }
-            }
-        }
-        prev = cur;
-#pragma unroll
-        for (int v = 0; v < CL_NV; ++v) {
-            xprev[v] = x[v];
-            accp[v] = accc[v];
-        }
-    }
+    march_strip_c<STAGE>(ca, blockIdx.x % a.nstrips, blockIdx.x / a.nstrips, threadIdx.x, dt, flag);
     if (STAGE == 2 && flag) atomicOr(&a.ctl->status, flag);
 }
 
@@ -539,9 +243,7 @@ __global__ void __launch_bounds__(128) k_closure_predict(ClosureArgs ca)
             for (int j = 0; j < 6; ++j) ca.pred[j * ca.pstride + i] = p[j];
         }
         if (WS) {
-            CRec r;
-            make_crec(r, x[0], 0.0f, x, p, false, false, a.hdry);
-            const float s = r.um + sqrtf(a.g * fmaxf(x[0], 0.0f) + r.s2) + r.s1;
+            const float s = closed_speed(x, p, a.g, a.hdry);
             if (i < nc) {
                 if (!(s <= 3.0e38f)) flag |= DEV_NAN;
                 if (!(x[0] >= 0.0f)) flag |= (x[0] < 0.0f) ? DEV_NEGDEPTH : DEV_NAN;
@@ -609,23 +311,30 @@ struct ClosureTC {
 };
 static_assert(sizeof(ClosureTC) % 16 == 0, "ClosureTC is copied in 16-byte words");
 
+// Tiles in flight per CTA.  With one, a CTA's epilogue waits for its own MMA and the other CTAs on
+// the SM fill that time (6 CTAs of 32 KB and 80 registers per thread, 24 warps per SM); with two,
+// each tile's epilogue overlaps the other tile's MMA (4 CTAs of 53 KB, 128 registers, 16 warps).
+constexpr int TC_TILES = 1;
+constexpr int TC_CHUNK = 16;  // accumulator columns read back per tensor-memory load batch
+// Every TC_POLY_EVERY-th pair of hidden activations takes its GELU from gelu_poly2 on the FMA pipe
+// instead of two tanh.approx on the SFU (0: none), balancing the two pipes.
+constexpr int TC_POLY_EVERY = 3;
+
 struct TCSmem {
     ClosureTC net;
-    alignas(128) uint16_t A1[2][128 * 16];  // layer-1 input tiles (K = 16), one per tile in flight
-    alignas(128) uint16_t A2[2][128 * 64];  // layer-2 and layer-3 input tiles (K = 64)
-    uint64_t bar[2];
+    alignas(128) uint16_t A1[TC_TILES][128 * 16];  // layer-1 input tiles (K = 16), one per tile in flight
+    alignas(128) uint16_t A2[TC_TILES][128 * 64];  // layer-2 and layer-3 input tiles (K = 64)
+    uint64_t bar[TC_TILES];
     uint32_t tmem;
 };
 
-// Two tiles are in flight per CTA: while the tensor core runs one tile's layer, the threads apply
-// the GELU to the other tile's previous layer.  Each tile owns a 64-column accumulator region that
-// serves its three layers in turn (a layer's accumulator is read back completely before the next
-// MMA into it is issued): 128 columns per CTA, 4 CTAs per SM (53 KB of shared memory each).
-constexpr uint32_t TC_COLS = 128;
+// Each tile owns a 64-column accumulator region that serves its three layers in turn (a layer's
+// accumulator is read back completely before the next MMA into it is issued).
+constexpr uint32_t TC_COLS = 64 * TC_TILES;
 constexpr long long TC_WAIT = 2000000000LL;    // ~1 s at 2 GHz
 constexpr int TC_DYN_SMEM = (int)sizeof(TCSmem);
 constexpr int TC_THREADS = 128;
-constexpr int TC_CTAS_PER_SM = 4;
+constexpr int TC_CTAS_PER_SM = TC_TILES == 1 ? 6 : 4;
 constexpr uint32_t TC_IDESC64 = tc::idesc_bf16_f32(128, 64);
 constexpr uint32_t TC_IDESC16 = tc::idesc_bf16_f32(128, 16);
 
@@ -645,13 +354,14 @@ __global__ void __launch_bounds__(TC_THREADS, TC_CTAS_PER_SM) k_closure_tc(Closu
         uint4 *dst = reinterpret_cast<uint4 *>(&sm.net);
         for (int i = tid; i < (int)(sizeof(ClosureTC) / 16); i += TC_THREADS) dst[i] = src[i];
         // columns 8..15 of the layer-1 inputs are zero padding for every tile
-        *reinterpret_cast<uint4 *>(&sm.A1[0][tc::kmajor_index(tid, 8, 16)]) = make_uint4(0u, 0u, 0u, 0u);
-        *reinterpret_cast<uint4 *>(&sm.A1[1][tc::kmajor_index(tid, 8, 16)]) = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int b = 0; b < TC_TILES; ++b)
+            *reinterpret_cast<uint4 *>(&sm.A1[b][tc::kmajor_index(tid, 8, 16)]) = make_uint4(0u, 0u, 0u, 0u);
     }
     if (warp == 0) tc::tmem_alloc(&sm.tmem, TC_COLS);
     if (tid == 0) {
-        tc::mbar_init(&sm.bar[0], 1);
-        tc::mbar_init(&sm.bar[1], 1);
+#pragma unroll
+        for (int b = 0; b < TC_TILES; ++b) tc::mbar_init(&sm.bar[b], 1);
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
@@ -659,16 +369,21 @@ __global__ void __launch_bounds__(TC_THREADS, TC_CTAS_PER_SM) k_closure_tc(Closu
     tc::fence_after_sync();
     const uint32_t tmem = sm.tmem;
     const uint32_t tlane = (uint32_t)(warp * 32) << 16;  // this warp's 32 lanes
+    // inside a step the launch is programmatic: the set-up above overlaps the previous kernel, whose
+    // results (the stage output, the control block) are read only after this
+    if (MODE != 2) pdl_enter();
     const bool skip = MODE != 2 && __syncthreads_or(tid == 0 && *(volatile unsigned int *)&a.ctl->status != 0u);
     const uint32_t sb1 = tc::smem_u32(sm.net.B1), sb2 = tc::smem_u32(sm.net.B2), sb3 = tc::smem_u32(sm.net.B3);
     const uint32_t sbb2 = tc::smem_u32(sm.net.Bb2), sbb3 = tc::smem_u32(sm.net.Bb3);
     const int64_t nc = MODE == 2 ? n : (int64_t)a.nx * a.ny;
     const int64_t ntiles = (nc + 127) / 128;
-    uint32_t phase[2] = {0u, 0u};
+    uint32_t phase[TC_TILES];
+#pragma unroll
+    for (int b = 0; b < TC_TILES; ++b) phase[b] = 0u;
     bool failed = false;
     float smax = 0.0f;
     unsigned flag = 0;
-    float x[2][CL_NV];  // the stage input of this thread's cells (wave speed)
+    float x[TC_TILES][CL_NV];  // the stage input of this thread's cells (wave speed)
 
     auto load = [&](int64_t tile, float *dst) {
         const int64_t i = tile * 128 + tid;
@@ -697,10 +412,14 @@ __global__ void __launch_bounds__(TC_THREADS, TC_CTAS_PER_SM) k_closure_tc(Closu
         *reinterpret_cast<uint4 *>(&sm.A1[b][tc::kmajor_index(tid, 0, 16)]) = w;
     };
     // the operand tiles written by all threads -> the tensor core; then one thread issues layer L of tile b
+    // the operand tiles written by all threads -> the tensor core; then one thread issues layer L of
+    // tile b.  The barrier also carries the outcome of the completion waits since the last one
+    // (false: some thread's wait gave up, stop).
+    bool lost = false;
     auto issue = [&](int b, int L) {
         tc::fence_async_smem();
         tc::fence_before_sync();
-        __syncthreads();
+        if (__syncthreads_or(lost)) return false;
         if (tid == 0) {
             tc::fence_after_sync();
             const uint32_t d = tmem + 64 * b;
@@ -718,36 +437,48 @@ __global__ void __launch_bounds__(TC_THREADS, TC_CTAS_PER_SM) k_closure_tc(Closu
             }
             tc::commit(&sm.bar[b]);
         }
-    };
-    auto wait = [&](int b) {
-        const bool ok = tc::mbar_wait(&sm.bar[b], phase[b], TC_WAIT);
-        if (__syncthreads_or(!ok)) return false;
-        phase[b] ^= 1u;
-        tc::fence_after_sync();
         return true;
+    };
+    // Every thread waits for its tile's MMAs itself (no barrier); a wait that gives up is recorded
+    // and stops the loop at the next barrier (its phase is kept for the final wait).
+    auto wait = [&](int b) {
+        if (tc::mbar_wait(&sm.bar[b], phase[b], TC_WAIT))
+            phase[b] ^= 1u;
+        else
+            lost = true;
+        tc::fence_after_sync();
     };
     // GELU of the 64 accumulator columns of tile b (which hold z/2, bias included) -> BF16 row of its
     // A2 tile.  The four loads are issued back to back and waited for once; with h = z/2,
     // GELU(z) = h (1 + tanh(h (2c + 8 * 0.044715 c h^2))), evaluated on packed FP32 pairs.
     auto hidden = [&](int b) {
-        uint32_t r[64];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) tc::tmem_ld16_nowait(tmem + tlane + 64 * b + 16 * c, r + 16 * c);
-        tc::wait_ld();
         const F2 kb(2.0f * 0.7978845608028654f), ka(8.0f * 0.044715f * 0.7978845608028654f);
 #pragma unroll
-        for (int g = 0; g < 8; ++g) {
-            uint32_t w[4];
+        for (int c0 = 0; c0 < 64; c0 += TC_CHUNK) {
+            uint32_t r[TC_CHUNK];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int j = 8 * g + 2 * q;
-                const F2 h(__uint_as_float(r[j]), __uint_as_float(r[j + 1]));
-                const F2 u = h * fma2(ka, h * h, kb);
-                const F2 t(tanh_approx(u.x()), tanh_approx(u.y()));
-                const F2 gz = fma2(h, t, h);
-                w[q] = pack_bf16(gz.x(), gz.y());
+            for (int c = 0; c < TC_CHUNK / 16; ++c) tc::tmem_ld16_nowait(tmem + tlane + 64 * b + c0 + 16 * c, r + 16 * c);
+            tc::wait_ld();
+#pragma unroll
+            for (int g = 0; g < TC_CHUNK / 8; ++g) {
+                uint32_t w[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int j = 8 * g + 2 * q;
+                    const F2 h(__uint_as_float(r[j]), __uint_as_float(r[j + 1]));
+                    F2 gz;
+                    if (TC_POLY_EVERY > 0 && (j / 2) % TC_POLY_EVERY == TC_POLY_EVERY - 1) {
+                        gz = gelu_poly2(h);  // this pair on the FMA pipe
+                    } else {
+                        const F2 u = h * fma2(ka, h * h, kb);
+                        const F2 t(tanh_approx(u.x()), tanh_approx(u.y()));
+                        gz = fma2(h, t, h);
+                    }
+                    w[q] = pack_bf16(gz.x(), gz.y());
+                }
+                *reinterpret_cast<uint4 *>(&sm.A2[b][tc::kmajor_index(tid, c0 + 8 * g, 64)]) =
+                    make_uint4(w[0], w[1], w[2], w[3]);
             }
-            *reinterpret_cast<uint4 *>(&sm.A2[b][tc::kmajor_index(tid, 8 * g, 64)]) = make_uint4(w[0], w[1], w[2], w[3]);
         }
     };
     // layer-3 accumulator of tile b -> outputs of this thread's cell
@@ -764,9 +495,7 @@ __global__ void __launch_bounds__(TC_THREADS, TC_CTAS_PER_SM) k_closure_tc(Closu
             for (int j = 0; j < 6; ++j) dst[j * stride + i] = p[j];
         }
         if (MODE == 1) {
-            CRec r;
-            make_crec(r, x[b][0], 0.0f, x[b], p, false, false, a.hdry);
-            const float sp = r.um + sqrtf(a.g * fmaxf(x[b][0], 0.0f) + r.s2) + r.s1;
+            const float sp = closed_speed(x[b], p, a.g, a.hdry);
             if (i < nc) {
                 if (!(sp <= 3.0e38f)) flag |= DEV_NAN;
                 if (!(x[b][0] >= 0.0f)) flag |= (x[b][0] < 0.0f) ? DEV_NEGDEPTH : DEV_NAN;
@@ -775,52 +504,73 @@ __global__ void __launch_bounds__(TC_THREADS, TC_CTAS_PER_SM) k_closure_tc(Closu
         }
     };
 
-    float inA[6], inB[6];
-    const int64_t npairs = (ntiles + 1) / 2;
-    if (!skip && blockIdx.x < npairs) load(2 * blockIdx.x, inA);
-    for (int64_t pr = blockIdx.x; pr < npairs && !skip; pr += gridDim.x) {
-        const int64_t tA = 2 * pr, tB = 2 * pr + 1;
-        const bool hasB = tB < ntiles;  // uniform across the CTA
-        if (hasB) load(tB, inB);
-        prep(0, inA);
-        issue(0, 1);
-        if (hasB) {
-            prep(1, inB);
-            issue(1, 1);
+    if constexpr (TC_TILES == 1) {
+        float in[6];
+        if (!skip && blockIdx.x < ntiles) load(blockIdx.x, in);
+        for (int64_t tile = blockIdx.x; tile < ntiles && !skip; tile += gridDim.x) {
+            prep(0, in);
+            if (!issue(0, 1)) break;
+            if (tile + gridDim.x < ntiles) load(tile + gridDim.x, in);  // the next tile's inputs
+            wait(0);
+            hidden(0);
+            if (!issue(0, 2)) break;
+            wait(0);
+            hidden(0);
+            if (!issue(0, 3)) break;
+            wait(0);
+            output(0, tile);
+            // every accumulator row is read before the next tile's layer-1 MMA overwrites the region
+            tc::fence_before_sync();
+            if (__syncthreads_or(lost)) break;
         }
-        if (pr + gridDim.x < npairs) load(2 * (pr + gridDim.x), inA);  // next pair's first tile
-        // layer 1 -> 2 -> 3 of both tiles, each epilogue overlapping the other tile's MMA
-        if (!wait(0)) { failed = true; break; }
-        hidden(0);
-        issue(0, 2);
-        if (hasB) {
-            if (!wait(1)) { failed = true; break; }
-            hidden(1);
-            issue(1, 2);
+    } else {
+        float inA[6], inB[6];
+        const int64_t npairs = (ntiles + 1) / 2;
+        if (!skip && blockIdx.x < npairs) load(2 * blockIdx.x, inA);
+        for (int64_t pr = blockIdx.x; pr < npairs && !skip; pr += gridDim.x) {
+            const int64_t tA = 2 * pr, tB = 2 * pr + 1;
+            const bool hasB = tB < ntiles;  // uniform across the CTA
+            if (hasB) load(tB, inB);
+            prep(0, inA);
+            if (!issue(0, 1)) break;
+            if (hasB) {
+                prep(1, inB);
+                if (!issue(1, 1)) break;
+            }
+            if (pr + gridDim.x < npairs) load(2 * (pr + gridDim.x), inA);  // next pair's first tile
+            // layer 1 -> 2 -> 3 of both tiles, each epilogue overlapping the other tile's MMA
+            wait(0);
+            hidden(0);
+            if (!issue(0, 2)) break;
+            if (hasB) {
+                wait(1);
+                hidden(1);
+                if (!issue(1, 2)) break;
+            }
+            wait(0);
+            hidden(0);
+            if (!issue(0, 3)) break;
+            if (hasB) {
+                wait(1);
+                hidden(1);
+                if (!issue(1, 3)) break;
+            }
+            wait(0);
+            output(0, tA);
+            if (hasB) {
+                wait(1);
+                output(1, tB);
+            }
+            tc::fence_before_sync();
+            if (__syncthreads_or(lost)) break;
         }
-        if (!wait(0)) { failed = true; break; }
-        hidden(0);
-        issue(0, 3);
-        if (hasB) {
-            if (!wait(1)) { failed = true; break; }
-            hidden(1);
-            issue(1, 3);
-        }
-        if (!wait(0)) { failed = true; break; }
-        output(0, tA);
-        if (hasB) {
-            if (!wait(1)) { failed = true; break; }
-            output(1, tB);
-        }
-        // every accumulator row is read before the next pair's layer-1 MMAs overwrite the regions
-        tc::fence_before_sync();
-        __syncthreads();
     }
+    failed = __syncthreads_or(lost);
     if (failed) {
         if (tid == 0) atomicOr(&a.ctl->status, DEV_TIMEOUT);
         // the MMAs still in flight, once more with a limit
-        tc::mbar_wait(&sm.bar[0], phase[0], TC_WAIT);
-        tc::mbar_wait(&sm.bar[1], phase[1], TC_WAIT);
+#pragma unroll
+        for (int b = 0; b < TC_TILES; ++b) tc::mbar_wait(&sm.bar[b], phase[b], TC_WAIT);
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -916,12 +666,13 @@ static cudaError_t launch_predict(zoomy_ctx *c, const ClosureArgs &ca, bool ws)
 {
     if (c->closure_engine == 0) {
         const unsigned grid = (unsigned)(TC_CTAS_PER_SM * c->nsm);
-        if (ws)
-            k_closure_tc<1><<<grid, TC_THREADS, TC_DYN_SMEM, c->stream>>>(ca, (const ClosureTC *)c->closure_tc, nullptr,
-                                                                   nullptr, 0);
-        else
-            k_closure_tc<0><<<grid, TC_THREADS, TC_DYN_SMEM, c->stream>>>(ca, (const ClosureTC *)c->closure_tc, nullptr,
-                                                                   nullptr, 0);
+        const ClosureTC *net = (const ClosureTC *)c->closure_tc;
+        const float *nof = nullptr;
+        float *noo = nullptr;
+        return ws ? launch_pdl_dyn(k_closure_tc<1>, grid, TC_THREADS, TC_DYN_SMEM, c->stream, ca, net, nof, noo,
+                                   (int64_t)0)
+                  : launch_pdl_dyn(k_closure_tc<0>, grid, TC_THREADS, TC_DYN_SMEM, c->stream, ca, net, nof, noo,
+                                   (int64_t)0);
     } else {
         const unsigned pgrid = (unsigned)(4 * c->nsm);
         if (ws)
@@ -955,15 +706,22 @@ zoomy_status closure_run_steps(zoomy_ctx *c, float *Q, int64_t ld, double dt, in
     a.dt_fixed = dt;
     a.ctl = c->ctl;
     a.nstrips = (int)((c->nx + 29) / 30);
-    a.H = c->rows_per_warp > 0 ? c->rows_per_warp : rows_per_warp_for(c->nx, c->ny, c->nsm, 16);
+    if (c->rows_per_warp > 0) {
+        a.H = c->rows_per_warp;
+    } else {  // segments of one wave of one-warp CTAs
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage_closure<2>, 32, 0) != cudaSuccess || nb < 1)
+            nb = 1;
+        const int64_t segs = std::max<int64_t>(1, (int64_t)c->nsm * nb / a.nstrips);
+        a.H = (int)std::max<int64_t>(1, (c->ny + segs - 1) / segs);
+    }
     a.nsegs = (int)((c->ny + a.H - 1) / a.H);
     ca.net = (const ClosureDev *)c->closure_d;
     ca.pred = (float *)c->closure_pred;
     ca.pstride = c->nx * c->ny;
     ca.lambda = (float)c->closure_lambda;
     float *Q1 = (float *)c->q1;
-    const int nwarps = a.nstrips * a.nsegs;
-    dim3 grid((nwarps + 3) / 4), block(128);
+    const dim3 grid((unsigned)(a.nstrips * a.nsegs)), block(32);
     for (int k = 0; k < nsteps; ++k) {
         // closure of Q^n and its wave speed (this step's dt) into slot k & 1, cleared by the previous
         // step's first stage (or at the start of the call)
@@ -979,20 +737,55 @@ zoomy_status closure_run_steps(zoomy_ctx *c, float *Q, int64_t ld, double dt, in
         a.Qn = Q;
         a.out = Q1;
         if ((ps = prof_mark(c, 1, true)) != ZOOMY_OK) return ps;
-        k_stage_closure<1><<<grid, block, 0, c->stream>>>(ca);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "closure stage 1 launch");
+        if ((e = launch_pdl(k_stage_closure<1>, grid, block, c->stream, ca)) != cudaSuccess)
+            return cuda_fail(e, "closure stage 1 launch");
         if ((ps = prof_mark(c, 1, false)) != ZOOMY_OK) return ps;
         a.X = Q1;
-        if ((ps = prof_mark(c, 3, true)) != ZOOMY_OK) return ps;
-        if ((e = launch_predict(c, ca, false)) != cudaSuccess) return cuda_fail(e, "closure prediction launch");
-        if ((ps = prof_mark(c, 3, false)) != ZOOMY_OK) return ps;
+        if (c->closure_schedule == 0) {  // schedule 1 keeps the predictions made on Q^n
+            if ((ps = prof_mark(c, 3, true)) != ZOOMY_OK) return ps;
+            if ((e = launch_predict(c, ca, false)) != cudaSuccess) return cuda_fail(e, "closure prediction launch");
+            if ((ps = prof_mark(c, 3, false)) != ZOOMY_OK) return ps;
+        }
         a.Qn = Q;
         a.out = Q;
         if ((ps = prof_mark(c, 2, true)) != ZOOMY_OK) return ps;
-        k_stage_closure<2><<<grid, block, 0, c->stream>>>(ca);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "closure stage 2 launch");
+        if ((e = launch_pdl(k_stage_closure<2>, grid, block, c->stream, ca)) != cudaSuccess)
+            return cuda_fail(e, "closure stage 2 launch");
         if ((ps = prof_mark(c, 2, false)) != ZOOMY_OK) return ps;
     }
+    return ZOOMY_OK;
+}
+
+// Maximum wave speed of the closed profiles of Q (the speed the closed solver's CFL step uses): the
+// prediction kernel with its wave-speed reduction into the auxiliary control block.
+zoomy_status closure_max_wavespeed(zoomy_ctx *c, const float *Q, int64_t ld, double *out)
+{
+    ClosureArgs ca;
+    memset(&ca, 0, sizeof(ca));
+    StageArgs<float> &a = ca.s;
+    a.X = Q;
+    a.ld = ld;
+    a.nx = (int)c->nx;
+    a.ny = (int)c->ny;
+    a.g = (float)c->g;
+    a.hdry = (float)c->hdry;
+    a.ctl = c->ctl_aux;
+    a.slot_out = 0;
+    ca.net = (const ClosureDev *)c->closure_d;
+    ca.pred = (float *)c->closure_pred;
+    ca.pstride = c->nx * c->ny;
+    ca.lambda = (float)c->closure_lambda;
+    cudaError_t e = cudaMemsetAsync(c->ctl_aux, 0, sizeof(DevCtl), c->stream);
+    if (e == cudaSuccess) e = launch_predict(c, ca, true);
+    DevCtl h;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, c->ctl_aux, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "closure wave speed");
+    float v;
+    memcpy(&v, &h.smax_f[0], 4);
+    *out = v;
+    if (h.status & DEV_NAN) return set_error(ZOOMY_ENAN, "non-finite state");
+    if (h.status & DEV_TIMEOUT) return set_error(ZOOMY_ETIMEOUT, "a device-side wait exceeded its limit");
     return ZOOMY_OK;
 }
 
@@ -1051,6 +844,13 @@ extern "C" zoomy_status zoomy_closure_eval(zoomy_ctx *c, const float *feat, floa
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "closure eval launch");
+    return ZOOMY_OK;
+}
+
+extern "C" zoomy_status zoomy_closure_schedule(zoomy_ctx *c, int32_t schedule)
+{
+    if (!c || schedule < 0 || schedule > 1) return set_error(ZOOMY_EINVAL, "zoomy_closure_schedule: schedule is 0 or 1");
+    c->closure_schedule = schedule;
     return ZOOMY_OK;
 }
 

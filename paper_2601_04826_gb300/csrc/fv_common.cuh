@@ -99,12 +99,13 @@ __device__ __forceinline__ void pdl_enter()
 }
 
 template <typename... KArgs, typename... Args>
-static inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args... args)
+static inline cudaError_t launch_pdl_dyn(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                         Args... args)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -112,6 +113,12 @@ static inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block,
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
+template <typename... KArgs, typename... Args>
+static inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args... args)
+{
+    return launch_pdl_dyn(k, grid, block, 0, st, args...);
 }
 
 template <typename T>

@@ -23,6 +23,7 @@ namespace zoomy {
 template <int N, int STAGE, bool IMP>
 __global__ void __launch_bounds__(32) k_stage_2d_f32(StageArgs<float> a)
 {
+    pdl_enter();  // launched with programmatic dependent launch: the previous kernel's results first
     if (*(volatile unsigned int *)&a.ctl->status) return;
     float dt;
     if (!step_dt(a, dt)) {
@@ -47,18 +48,12 @@ static cudaError_t launch_f32(const StageArgs<float> &a, int stage, int wpb, cud
     if (!a.bed) return cudaErrorInvalidValue;
     if (stage == 2 && a.Qn != a.out) return cudaErrorInvalidValue;  // stage 2 updates Q^n in place
     dim3 grid(a.nstrips * a.nsegs), block(32);
-    if (a.src_implicit) {
-        if (stage == 1)
-            k_stage_2d_f32<N, 1, true><<<grid, block, 0, st>>>(a);
-        else
-            k_stage_2d_f32<N, 2, true><<<grid, block, 0, st>>>(a);
-    } else {
-        if (stage == 1)
-            k_stage_2d_f32<N, 1, false><<<grid, block, 0, st>>>(a);
-        else
-            k_stage_2d_f32<N, 2, false><<<grid, block, 0, st>>>(a);
-    }
-    return cudaGetLastError();
+    // each launch overlaps its ramp with the previous kernel's tail (programmatic dependent launch)
+    if (a.src_implicit)
+        return stage == 1 ? launch_pdl(k_stage_2d_f32<N, 1, true>, grid, block, st, a)
+                          : launch_pdl(k_stage_2d_f32<N, 2, true>, grid, block, st, a);
+    return stage == 1 ? launch_pdl(k_stage_2d_f32<N, 1, false>, grid, block, st, a)
+                      : launch_pdl(k_stage_2d_f32<N, 2, false>, grid, block, st, a);
 }
 
 cudaError_t launch_stage_2d_f32(int level, const StageArgs<float> &a, int stage, int wpb, cudaStream_t st)

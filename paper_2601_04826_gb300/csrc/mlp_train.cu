@@ -11,6 +11,7 @@
 //              fixed order: deterministic)
 //   update:    Adam, element-wise
 #include <cmath>
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <new>
@@ -380,3 +381,79 @@ extern "C" zoomy_status zoomy_closure_samples(const float *Q, int64_t ld, int32_
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? ZOOMY_OK : cuda_fail(e, "closure samples launch");
 }
+
+// Per-column maxima of |X| and |T| ([n][6] each) into max_x / max_t (device [6], zeroed by the
+// caller): the bit patterns of non-negative floats order like unsigned integers.
+__global__ void k_sample_absmax(const float *X, const float *T, int64_t n, unsigned *max_x, unsigned *max_t)
+{
+    __shared__ unsigned sx[6], st[6];
+    if (threadIdx.x < 6) sx[threadIdx.x] = st[threadIdx.x] = 0u;
+    __syncthreads();
+    unsigned mx[6] = {0, 0, 0, 0, 0, 0}, mt[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            mx[j] = max(mx[j], __float_as_uint(fabsf(X[i * 6 + j])));
+            mt[j] = max(mt[j], __float_as_uint(fabsf(T[i * 6 + j])));
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        atomicMax(&sx[j], mx[j]);
+        atomicMax(&st[j], mt[j]);
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        atomicMax(&max_x[threadIdx.x], sx[threadIdx.x]);
+        atomicMax(&max_t[threadIdx.x], st[threadIdx.x]);
+    }
+}
+
+__global__ void k_sample_scale(float *X, float *T, int64_t n, const float *in_scale, const float *out_scale)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n * 6; i += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(i % 6);
+        X[i] = __fmul_rn(X[i], in_scale[j]);
+        T[i] = __fdiv_rn(T[i], out_scale[j]);  // IEEE division (the library builds with fast math)
+    }
+}
+
+extern "C" zoomy_status zoomy_sample_scales(const float *X, const float *T, int64_t n, float *in_scale,
+                                            float *out_scale, void *stream)
+{
+    if (!X || !T || !in_scale || !out_scale || n < 1) return set_error(ZOOMY_EINVAL, "zoomy_sample_scales: bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned *d = nullptr;
+    cudaError_t e = cudaMallocAsync(&d, 12 * sizeof(unsigned), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+    unsigned h[12];
+    if ((e = cudaMemsetAsync(d, 0, 12 * sizeof(unsigned), st)) == cudaSuccess) {
+        const int64_t blocks = std::min<int64_t>((n + 255) / 256, 1024);
+        k_sample_absmax<<<(unsigned)blocks, 256, 0, st>>>(X, T, n, d, d + 6);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    cudaFreeAsync(d, st);
+    if (e != cudaSuccess) return cuda_fail(e, "zoomy_sample_scales");
+    for (int j = 0; j < 6; ++j) {
+        float mx, mt;
+        memcpy(&mx, &h[j], 4);
+        memcpy(&mt, &h[6 + j], 4);
+        in_scale[j] = 1.0f / std::max(mx, 1e-12f);
+        out_scale[j] = std::max(mt, 1e-12f);
+    }
+    return ZOOMY_OK;
+}
+
+extern "C" zoomy_status zoomy_sample_scale(float *X, float *T, int64_t n, const float *in_scale, const float *out_scale,
+                                           void *stream)
+{
+    if (!X || !T || !in_scale || !out_scale || n < 0) return set_error(ZOOMY_EINVAL, "zoomy_sample_scale: bad arguments");
+    if (n == 0) return ZOOMY_OK;
+    const int64_t blocks = std::min<int64_t>((6 * n + 255) / 256, 4096);
+    k_sample_scale<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(X, T, n, in_scale, out_scale);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? ZOOMY_OK : cuda_fail(e, "sample scale launch");
+}
+

@@ -378,6 +378,7 @@ extern "C" zoomy_status zoomy_max_wavespeed(zoomy_ctx *c, const void *Q, int64_t
     if (st != ZOOMY_OK) return st;
     if (c->vam) return set_error(ZOOMY_EINVAL, "zoomy_max_wavespeed: not defined for the VAM model");
     if (!out) return set_error(ZOOMY_EINVAL, "zoomy_max_wavespeed: NULL output");
+    if (c->closure_on) return closure_max_wavespeed(c, (const float *)Q, ld, out);
     ZCHECK(cudaMemsetAsync(c->ctl_aux, 0, sizeof(DevCtl), c->stream));
     cudaError_t e = c->dtype == ZOOMY_FP64
                         ? launch_wavespeed<double>(c->dim, c->level, (const double *)Q, ld, c->nc, c->g, c->hdry,
@@ -398,6 +399,45 @@ extern "C" zoomy_status zoomy_max_wavespeed(zoomy_ctx *c, const void *Q, int64_t
         *out = v;
     }
     if (h.status & DEV_NAN) return set_error(ZOOMY_ENAN, "non-finite state");
+    return ZOOMY_OK;
+}
+
+// Advance to t_end with CFL steps in chunks (one wave-speed read per chunk) and land on t_end exactly:
+// once fewer than ~1.25 CFL steps remain, one or two fixed steps of equal length finish the run.
+extern "C" zoomy_status zoomy_advance(zoomy_ctx *c, void *Q, int64_t ld, double t_end, int32_t chunk, double *t_out,
+                                      int64_t *steps_out)
+{
+    zoomy_status st = check_step_args(c, Q, ld, 0.0, 0, "zoomy_advance");
+    if (st != ZOOMY_OK) return st;
+    if (!(t_end >= 0.0) || !(t_end < 1e300) || chunk < 1)
+        return set_error(ZOOMY_EINVAL, "zoomy_advance: need a finite t_end >= 0 and chunk >= 1");
+    double t = 0.0;
+    int64_t steps = 0;
+    while (t_end - t > 1e-12 * t_end) {
+        const double rem = t_end - t;
+        double smax = 0.0;
+        if ((st = zoomy_max_wavespeed(c, Q, ld, &smax)) != ZOOMY_OK) return st;
+        if (!(smax > 0.0)) return set_error(ZOOMY_ECFL, "zoomy_advance: no positive finite wave speed");
+        const double dt_est = c->cfl * c->min_delta / smax;
+        const double want = 0.8 * rem / dt_est - 1.0;
+        const int n = want >= (double)chunk ? chunk : (int)want;
+        double dt_sum = 0.0;
+        if (n >= 1) {
+            if ((st = zoomy_step(c, Q, ld, 0.0, n, &dt_sum)) != ZOOMY_OK) return st;
+            t += dt_sum;
+            steps += n;
+        } else {
+            const int k = rem <= dt_est ? 1 : 2;
+            for (int i = 0; i < k; ++i) {
+                if ((st = zoomy_step(c, Q, ld, rem / k, 1, &dt_sum)) != ZOOMY_OK) return st;
+                t += dt_sum;
+            }
+            steps += k;
+            break;
+        }
+    }
+    if (t_out) *t_out = t;
+    if (steps_out) *steps_out = steps;
     return ZOOMY_OK;
 }
 

@@ -56,6 +56,7 @@ struct zoomy_ctx {
     void *closure_pred = nullptr;  // predicted closed moments of the current stage input [6][nx ny]
     void *closure_tc = nullptr;    // the network in the tcgen05 operand layout
     int closure_engine = 0;        // 0: tcgen05 (tensor memory), 1: mma.sync
+    int closure_schedule = 0;      // 0: network on every stage input, 1: once per step on Q^n
     bool closure_on = false;
     double closure_lambda = 0.0;
     // ensemble (fv_ensemble.cu)
@@ -99,6 +100,7 @@ void tri_free(zoomy_ctx *c);
 void ens_free(zoomy_ctx *c);
 // learned closure (fv_closure.cu)
 zoomy_status closure_run_steps(zoomy_ctx *c, float *Q, int64_t ld, double dt, int nsteps);
+zoomy_status closure_max_wavespeed(zoomy_ctx *c, const float *Q, int64_t ld, double *out);
 // VAM predictor-corrector (vam.cu)
 zoomy_status vam_run_steps(zoomy_ctx *c, double *Q, int64_t ld, double dt, int nsteps);
 zoomy_status closure_upload(zoomy_ctx *c, const float *params, const float *in_scale, const float *out_scale);

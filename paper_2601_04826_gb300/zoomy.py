@@ -89,6 +89,12 @@ _SIGNATURES = [
     ("zoomy_ensemble_set_barrier", C.c_int, [C.c_void_p, C.c_int64, C.c_int32]),
     ("zoomy_profile_enable", C.c_int, [C.c_void_p, C.c_int32]),
     ("zoomy_profile_read", C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
+    ("zoomy_closure_schedule", C.c_int, [C.c_void_p, C.c_int32]),
+    ("zoomy_advance", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_int32, C.POINTER(C.c_double),
+                                C.POINTER(C.c_int64)]),
+    ("zoomy_sample_scales", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_float),
+                                      C.POINTER(C.c_float), C.c_void_p]),
+    ("zoomy_sample_scale", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("zoomy_step_noalloc", C.c_int, [C.c_int64, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_double,
                                      C.POINTER(C.c_int32), C.c_int32, C.POINTER(zoomy_friction), C.c_double,
                                      C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_int64, C.c_double,
@@ -367,6 +373,28 @@ def zoomy_step_noalloc(nx, ny, x0, x1, y0, y1, bc, level, friction, g, cfl, h_dr
     return t.value if sync else None
 
 
+def zoomy_advance(ctx, Q, ld, t_end, chunk=256):
+    t = C.c_double()
+    n = C.c_int64()
+    _check(lib().zoomy_advance(ctx, _ptr(Q), ld, t_end, chunk, C.byref(t), C.byref(n)))
+    return t.value, n.value
+
+
+def zoomy_sample_scales(X, T, n, stream=None):
+    ins = (C.c_float * 6)()
+    outs = (C.c_float * 6)()
+    _check(lib().zoomy_sample_scales(_ptr(X), _ptr(T), n, ins, outs, _stream(stream)))
+    return list(ins), list(outs)
+
+
+def zoomy_sample_scale(X, T, n, in_scale, out_scale, stream=None):
+    _check(lib().zoomy_sample_scale(_ptr(X), _ptr(T), n, _ptr(in_scale), _ptr(out_scale), _stream(stream)))
+
+
+def zoomy_closure_schedule(ctx, schedule):
+    _check(lib().zoomy_closure_schedule(ctx, schedule))
+
+
 def zoomy_last_error():
     return lib().zoomy_last_error().decode()
 
@@ -452,6 +480,10 @@ class Context:
 
     def step_host(self, Q_host, nsteps=1, dt=0.0):
         return zoomy_step_host(self.ctx, Q_host, Q_host.stride(0), dt, nsteps)
+
+    def advance(self, Q, t_end, chunk=256):
+        """CFL steps to t_end exactly (zoomy_advance): returns (time advanced, steps)."""
+        return zoomy_advance(self.ctx, Q, self._ld(Q), t_end, chunk)
 
     def max_wavespeed(self, Q):
         return zoomy_max_wavespeed(self.ctx, Q, self._ld(Q))

@@ -147,21 +147,31 @@ def test_training_is_deterministic(Z):
                                           T.astype(np.float64))[0]
 
 
-def test_trained_closure_beats_level1(Z):
-    """Train on 32 level-4 runs (64^2), then three held-out members: relative L1 error of h, h u_m,
-    h v_m at T = 2 against level 4, for plain level 1 and for the closed level 1."""
+@pytest.fixture(scope="module")
+def trained(Z):
+    """A closure trained on 32 level-4 runs (64^2) to T = 2, shared by the gain tests."""
     from paper_2601_04826_gb300 import closure
 
-    side, T = 64, 2.0
-    F, Y, _ = closure.generate_samples(nmembers=32, side=side, level=4, T=T, snapshots=8, seed=3)
+    F, Y, _ = closure.generate_samples(nmembers=32, side=64, level=4, T=2.0, snapshots=8, seed=3)
     ins, outs = closure.scales(F, Y)
     params, hist = closure.fit(F, Y, ins, outs, steps=3000, batch=16384, seed=0)
     print("training loss", hist)
+    return params, ins, outs
+
+
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_trained_closure_beats_level1(Z, trained, schedule):
+    """Three held-out members: relative L1 error of h, h u_m, h v_m at T = 2 against level 4, for plain
+    level 1 and for the closed level 1 (network on every stage input, or once per step)."""
+    from paper_2601_04826_gb300 import closure
+
+    side, T = 64, 2.0
+    params, ins, outs = trained
     _, lam, seeds = inputs.ensemble_members(3, seed=4242)
     e1s, ecs = [], []
     for m in range(3):
         runs = {"l4": closure.Run(side, 4, lam[m], seeds[m]), "l1": closure.Run(side, 1, lam[m], seeds[m]),
-                "cl": closure.Run(side, 1, lam[m], seeds[m], closure=(params, ins, outs))}
+                "cl": closure.Run(side, 1, lam[m], seeds[m], closure=(params, ins, outs), schedule=schedule)}
         out = {}
         for k, r in runs.items():
             r.run_to(T)
@@ -174,3 +184,20 @@ def test_trained_closure_beats_level1(Z):
         ecs.append(err["cl"])
         assert err["cl"][0] < 0.5 * err["l1"][0]
     assert np.sum(ecs) < np.sum(e1s)
+
+
+def test_sample_scales_and_scaling(Z):
+    """zoomy_sample_scales: 1 / max|X| and max|T| per column; zoomy_sample_scale applies them in place."""
+    import torch
+
+    rng = np.random.default_rng(5)
+    n = 100003
+    X = rng.normal(size=(n, 6)).astype(np.float32) * np.array([1, 2, 3, 0.5, 0.25, 7], dtype=np.float32)
+    T = rng.normal(size=(n, 6)).astype(np.float32) * np.array([0.1, 0.2, 3, 5, 0.01, 1], dtype=np.float32)
+    Xd, Td = torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda")
+    ins, outs = Z.zoomy_sample_scales(Xd, Td, n)
+    np.testing.assert_array_equal(np.float32(ins), np.float32(1.0) / np.abs(X).max(axis=0))
+    np.testing.assert_array_equal(np.float32(outs), np.abs(T).max(axis=0))
+    Z.zoomy_sample_scale(Xd, Td, n, torch.tensor(ins, device="cuda"), torch.tensor(outs, device="cuda"))
+    np.testing.assert_array_equal(Xd.cpu().numpy(), X * np.float32(ins))
+    np.testing.assert_array_equal(Td.cpu().numpy(), T / np.float32(outs))
