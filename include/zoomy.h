@@ -46,7 +46,9 @@ typedef enum {
     ZOOMY_ENEGDEPTH = 5,  /* a step produced a negative depth */
     ZOOMY_ECFL = 6,       /* no positive finite wave speed: the CFL step is undefined */
     ZOOMY_ETIMEOUT = 7,   /* a device-side wait gave up (persistent ensemble kernel) */
-    ZOOMY_ESTATE = 8      /* call out of order (e.g. zoomy_step before zoomy_model_set) */
+    ZOOMY_ESTATE = 8,     /* call out of order (e.g. zoomy_step before zoomy_model_set) */
+    ZOOMY_EBOUNDS = 9     /* bounds-checking build only: a kernel met a gather index outside its buffer
+                             (the access was redirected to element 0 and flagged) */
 } zoomy_status;
 
 typedef struct zoomy_ctx zoomy_ctx; /* opaque, library-owned */

@@ -16,6 +16,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libzoomy.so")
+# bounds-checking build: every gather index of the kernels checked before its access
+DEBUG_BUILD = os.path.join(HERE, "_build_debug")
+DEBUG_LIB = os.path.join(HERE, "libzoomy_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-use_fast_math",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"] + ARCH
@@ -38,12 +41,12 @@ def headers():
     return hs
 
 
-def _compile(src, verbose=False):
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src, verbose=False, debug=False):
+    obj = os.path.join(DEBUG_BUILD if debug else BUILD, os.path.basename(src) + ".o")
     newest_dep = max(os.path.getmtime(p) for p in [src] + headers())
     if os.path.exists(obj) and os.path.getmtime(obj) >= newest_dep:
         return obj, ""
-    cmd = [nvcc(), *NVCC_FLAGS, "-c", src, "-o", obj + ".tmp"]
+    cmd = [nvcc(), *NVCC_FLAGS, *(["-DZOOMY_BOUNDS_CHECK"] if debug else []), "-c", src, "-o", obj + ".tmp"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -53,25 +56,28 @@ def _compile(src, verbose=False):
     return obj, r.stderr
 
 
-def build(verbose: bool = False, jobs: int | None = None) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, jobs: int | None = None, debug: bool = False) -> str:
+    """Build libzoomy.so, or with debug=True the bounds-checking libzoomy_debug.so (compiled with
+    -DZOOMY_BOUNDS_CHECK; load it by setting ZOOMY_LIBRARY to its path)."""
+    bdir, lib = (DEBUG_BUILD, DEBUG_LIB) if debug else (BUILD, LIB)
+    os.makedirs(bdir, exist_ok=True)
     srcs = sources()
-    with cf.ThreadPoolExecutor(max_workers=jobs or min(8, os.cpu_count() or 4)) as ex:
-        results = list(ex.map(lambda s: _compile(s, verbose), srcs))
+    with cf.ThreadPoolExecutor(max_workers=jobs or min(16, os.cpu_count() or 4)) as ex:
+        results = list(ex.map(lambda s: _compile(s, verbose, debug), srcs))
     objs = [o for o, _ in results]
     if verbose:
         for _, log in results:
             if log:
                 sys.stderr.write(log)
-    if os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(o) for o in objs):
-        return LIB
-    cmd = [nvcc(), *ARCH, "-shared", "-o", LIB + ".tmp", *objs, "-lcudart_static", "-lrt", "-lpthread", "-ldl"]
+    if os.path.exists(lib) and os.path.getmtime(lib) >= max(os.path.getmtime(o) for o in objs):
+        return lib
+    cmd = [nvcc(), *ARCH, "-shared", "-o", lib + ".tmp", *objs, "-lcudart_static", "-lrt", "-lpthread", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(LIB + ".tmp", LIB)
-    return LIB
+    os.replace(lib + ".tmp", lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv))
+    print(build(verbose="-v" in sys.argv, debug="--debug" in sys.argv))

@@ -225,10 +225,10 @@ struct RowCtxC {
 // raw row: 5 state values, bed, 6 predictions
 constexpr int CL_RAW = CL_NV + 1 + 6;
 
-__device__ __forceinline__ void load_row_c(const RowCtxC &c, int r, float *dst)
+__device__ __forceinline__ void load_row_c(const RowCtxC &c, int r, float *dst, unsigned *status)
 {
     const int rs = r < 0 ? 0 : (r >= c.ny ? c.ny - 1 : r);
-    const int off = rs * c.nx;
+    const int off = (int)bounds_idx(rs * c.nx + c.csrc, (int64_t)c.nx * c.ny, status) - c.csrc;
 #pragma unroll
     for (int v = 0; v < CL_NV; ++v) dst[v] = __ldg(c.xcol + (off + v * c.ld));
     dst[CL_NV] = __ldg(c.bcol + off);
@@ -263,7 +263,7 @@ __device__ __forceinline__ void row_body_c(const StageArgs<float> &a, const RowC
         C.acc[3] = fmaf(dt * f, xa, nxt[3]);
         C.acc[4] = fmaf(dt * f, xb, nxt[4]);
     }
-    if (STEADY || r < r1) load_row_c(c, r + 1, nxt);
+    if (STEADY || r < r1) load_row_c(c, r + 1, nxt, &a.ctl->status);
     const bool xrow = STEADY || (r >= r0 && r < r1);
     const bool fin = STEADY || (r - 1 >= r0 && r - 1 < r1);
     // stage 2 updates Q^n in place: Q^n of the finished row comes from the addresses it is stored to
@@ -394,16 +394,18 @@ __device__ __forceinline__ void march_strip_c(const ClosureArgs &ca, int strip, 
     zero_row_c(A);
     zero_row_c(B);
     float nxt[CL_RAW];
-    load_row_c(c, r0 - 1, nxt);
+    load_row_c(c, r0 - 1, nxt, &a.ctl->status);
     int r = r0 - 1;
-    row_body_c<STAGE>(a, c, r, r0, r1, dt, nxt, B, A, flag);
-    row_body_c<STAGE>(a, c, r + 1, r0, r1, dt, nxt, A, B, flag);
-    for (r = r0 + 1; r + 1 < r1; r += 2) {
-        row_body_c<STAGE, true>(a, c, r, r0, r1, dt, nxt, B, A, flag);
-        row_body_c<STAGE, true>(a, c, r + 1, r0, r1, dt, nxt, A, B, flag);
+    while (true) {  // general pairs at both ends of the segment, branch-free pairs inside it
+        row_body_c<STAGE>(a, c, r, r0, r1, dt, nxt, B, A, flag);
+        if (r + 1 <= r1) row_body_c<STAGE>(a, c, r + 1, r0, r1, dt, nxt, A, B, flag);
+        r += 2;
+        if (r > r1) break;
+        for (; r + 1 < r1; r += 2) {
+            row_body_c<STAGE, true>(a, c, r, r0, r1, dt, nxt, B, A, flag);
+            row_body_c<STAGE, true>(a, c, r + 1, r0, r1, dt, nxt, A, B, flag);
+        }
     }
-    if (r <= r1) row_body_c<STAGE>(a, c, r, r0, r1, dt, nxt, B, A, flag);
-    if (r + 1 <= r1) row_body_c<STAGE>(a, c, r + 1, r0, r1, dt, nxt, A, B, flag);
 }
 
 }  // namespace zoomy

@@ -18,7 +18,22 @@ struct DevCtl {
     unsigned int pad;
 };
 
-enum : unsigned int { DEV_NAN = 1u, DEV_NEGDEPTH = 2u, DEV_NOWAVE = 4u };
+enum : unsigned int { DEV_NAN = 1u, DEV_NEGDEPTH = 2u, DEV_NOWAVE = 4u, DEV_BOUNDS = 16u };
+
+// Bounds-checking build (compiled with -DZOOMY_BOUNDS_CHECK, build(debug=True)): every gather index
+// of the stage, lifting and VAM kernels passes through bounds_idx before its access.  An index
+// outside [0, n) sets DEV_BOUNDS in the control block (the host returns ZOOMY_EBOUNDS) and is replaced
+// by 0, so the access itself stays inside the buffer.  Regular builds compile the check away.
+#ifdef ZOOMY_BOUNDS_CHECK
+__device__ __forceinline__ int64_t bounds_idx(int64_t i, int64_t n, unsigned *status)
+{
+    if (i >= 0 && i < n) return i;
+    atomicOr(status, DEV_BOUNDS);
+    return 0;
+}
+#else
+__device__ __forceinline__ int64_t bounds_idx(int64_t i, int64_t, unsigned *) { return i; }
+#endif
 
 // Variable index of h alpha_k / h beta_k in the SoA state (Eq. (sme) variable order).
 template <int N, int D>

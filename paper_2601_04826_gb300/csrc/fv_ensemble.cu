@@ -43,6 +43,7 @@ struct EnsArgs {
     unsigned *bar;          // grid barrier: [0] arrivals, [1] generation
     unsigned *gstatus;      // launch-wide status (timeout)
     unsigned nbar;          // participants of the barrier (grid size + extra, see zoomy_ensemble_set_barrier)
+    int64_t ncells;         // cells of all members (the concatenated arrays' extent)
     long long spin_limit;   // barrier spin iterations before giving up
 };
 
@@ -53,6 +54,8 @@ __device__ __forceinline__ StageArgs<float> member_args(const EnsArgs &e, int m,
 {
     StageArgs<float> a = e.base;
     const EnsMember mb = e.mem[m];
+    // the member's cells lie inside the concatenated arrays (its last cell is checked)
+    (void)bounds_idx(mb.off + (int64_t)mb.side * mb.side - 1, e.ncells, &e.ctls[m].status);
     a.X = (stage == 2 ? e.Q1 : e.Q) + mb.off;
     a.Qn = e.Q + mb.off;
     a.out = (stage == 1 ? e.Q1 : e.Q) + mb.off;
@@ -119,11 +122,11 @@ __device__ __forceinline__ void run_item(const EnsArgs &e, int idx, int phase, i
         if (it.y == 0 && it.z == 0 && lane == 0) step_bookkeeping(a, dt);
         float smax = 0.0f;
         unsigned flag = 0;
-        march_strip<N, 1>(a, it.y, it.z, lane, dt, smax, flag);
+        march_strip<N, 1, false, false>(a, it.y, it.z, lane, dt, smax, flag);
     } else {
         float smax = 0.0f;
         unsigned flag = 0;
-        march_strip<N, 2>(a, it.y, it.z, lane, dt, smax, flag);
+        march_strip<N, 2, false, false>(a, it.y, it.z, lane, dt, smax, flag);
         if (flag) atomicOr(&a.ctl->status, flag);
         reduce_smax<float>(a.ctl, a.slot_out, smax);
     }
@@ -299,6 +302,7 @@ static EnsArgs ens_args(zoomy_ctx *c, float *Q, float *Q1, int64_t ld, int nstep
     a.items = E->items_d;
     a.nitems = E->nitems;
     a.nmembers = (int)E->mem.size();
+    a.ncells = c->nc;
     a.nsteps = nsteps;
     a.ctls = E->ctls_d;
     a.counters = E->counters_d;

@@ -40,7 +40,7 @@ __device__ __forceinline__ void state_at(const StageArgs<T> &a, int ix, int iy, 
     constexpr int m = N + 1, nv = O2<N, D>::nv;
     const int cx = ix < 0 ? 0 : (ix >= a.nx ? a.nx - 1 : ix);
     const int cy = D == 1 ? 0 : (iy < 0 ? 0 : (iy >= a.ny ? a.ny - 1 : iy));
-    const int64_t idx = (int64_t)cy * a.nx + cx;
+    const int64_t idx = bounds_idx((int64_t)cy * a.nx + cx, (int64_t)a.nx * (D == 1 ? 1 : a.ny), &a.ctl->status);
 #pragma unroll
     for (int v = 0; v < nv; ++v) q[v] = a.X[(int64_t)v * a.ld + idx];
     q[nv] = a.bed[idx];

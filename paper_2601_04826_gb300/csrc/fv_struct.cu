@@ -22,7 +22,7 @@ template <int N, typename T>
 __device__ __forceinline__ void load_cell_1d(const StageArgs<T> &a, int i, CellRec<N, 1, T> &r, T *raw)
 {
     constexpr int m = N + 1;
-    int src = i < 0 ? 0 : (i >= a.nx ? a.nx - 1 : i);
+    const int src = (int)bounds_idx(i < 0 ? 0 : (i >= a.nx ? a.nx - 1 : i), a.nx, &a.ctl->status);
     bool wall = (i < 0 && a.bc[0] == 1) || (i >= a.nx && a.bc[1] == 1);
     T h = a.X[src];
     T ha[m];
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(128) k_stage_2d(StageArgs<T> a)
     for (int r = r0 - 1; r <= r1; ++r) {
         const int rsrc = r < 0 ? 0 : (r >= a.ny ? a.ny - 1 : r);
         const bool ywall = (r < 0 && a.bc[2] == 1) || (r >= a.ny && a.bc[3] == 1);
-        const int64_t cidx = (int64_t)rsrc * a.nx + csrc;
+        const int64_t cidx = bounds_idx((int64_t)rsrc * a.nx + csrc, (int64_t)a.nx * a.ny, &a.ctl->status);
         // load the stage input of this row (ghost rows/columns mirror the boundary cell)
 #pragma unroll
         for (int v = 0; v < nv; ++v) xcur[v] = a.X[(int64_t)v * a.ld + cidx];

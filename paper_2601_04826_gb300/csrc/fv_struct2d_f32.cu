@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(32) k_stage_2d_f32(StageArgs<float> a)
     // one warp per CTA: the strip / segment indices and the row loop are uniform across the CTA
     float smax = 0.0f;
     unsigned flag = 0;
-    march_strip<N, STAGE, IMP>(a, blockIdx.x % a.nstrips, blockIdx.x / a.nstrips, threadIdx.x, dt, smax, flag);
+    march_strip<N, STAGE, IMP, !IMP>(a, blockIdx.x % a.nstrips, blockIdx.x / a.nstrips, threadIdx.x, dt, smax, flag);
     if (STAGE == 2) {
         if (flag) atomicOr(&a.ctl->status, flag);
         reduce_smax<float>(a.ctl, a.slot_out, smax);

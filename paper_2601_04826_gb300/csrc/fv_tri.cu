@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(128) k_stage_tri(TriArgs a)
         }
         float rawn[3][nv + 1];
 #pragma unroll
-        for (int f = 0; f < 3; ++f) tri_load<N>(a, jn[f] >= 0 ? jn[f] : i, rawn[f]);
+        for (int f = 0; f < 3; ++f) tri_load<N>(a, bounds_idx(jn[f] >= 0 ? jn[f] : i, a.nc, &s.ctl->status), rawn[f]);
         float acc[nv];
 #pragma unroll
         for (int v = 0; v < nv; ++v) acc[v] = 0.0f;

@@ -38,6 +38,7 @@ struct LiftArgs {
     const int32_t *nbr;  // triangles: [3][nc]
     const float *geo;    // triangles: nx[3][nc], ny[3][nc], |e|/|Omega| [3][nc]
     int K;
+    unsigned *status;    // bounds-checking build: the context's status word
 };
 
 // MESH 0: 1D uniform, 1: 2D structured, 2: triangles
@@ -53,7 +54,10 @@ __global__ void __launch_bounds__(128) k_lift3d(LiftArgs<T> a)
         T gx[nv + 1], gy[nv + 1];
 #pragma unroll
         for (int v = 0; v <= nv; ++v) gx[v] = gy[v] = T(0);
-        auto val = [&](int64_t j, int v) { return v < nv ? a.Q[v * a.ld + j] : a.bed[j]; };
+        auto val = [&](int64_t j, int v) {
+            j = bounds_idx(j, a.nc, a.status);
+            return v < nv ? a.Q[v * a.ld + j] : a.bed[j];
+        };
         if (MESH == 0 || MESH == 1) {
             const int64_t ix = MESH == 0 ? i : i % a.nx;
             const int64_t iw = ix > 0 ? i - 1 : i, ie = ix + 1 < a.nx ? i + 1 : i;
@@ -180,13 +184,19 @@ static zoomy_status lift_run(zoomy_ctx *c, const T *Q, int64_t ld, int K, const 
     a.nbr = c->tri_nbr_d;
     a.geo = c->tri_geo_d;
     a.K = K;
+    a.status = &c->ctl->status;
     if (c->kind == ZOOMY_MESH_1D)
         e = launch_lift_mesh<0, T>(c->level, a, c->nsm, c->stream);
     else if (c->kind == ZOOMY_MESH_2D)
         e = launch_lift_mesh<1, T>(c->level, a, c->nsm, c->stream);
     else
         e = launch_lift_mesh<2, T>(c->level, a, c->nsm, c->stream);
-    return e == cudaSuccess ? ZOOMY_OK : cuda_fail(e, "zoomy_lift3d launch");
+    if (e != cudaSuccess) return cuda_fail(e, "zoomy_lift3d launch");
+#ifdef ZOOMY_BOUNDS_CHECK
+    return read_status(c, nullptr);  // the bounds-checking build reports a bad index right away
+#else
+    return ZOOMY_OK;
+#endif
 }
 
 }  // namespace zoomy

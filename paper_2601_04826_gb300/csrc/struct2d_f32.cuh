@@ -273,7 +273,7 @@ __device__ __forceinline__ void load_row(const StageArgs<float> &a, const RowCtx
 {
     constexpr int nv = 3 + 2 * N;
     const int rs = r < 0 ? 0 : (r >= c.ny ? c.ny - 1 : r);
-    const int off = rs * c.nx;
+    const int off = (int)bounds_idx(rs * c.nx + c.csrc, (int64_t)c.nx * c.ny, &a.ctl->status) - c.csrc;
 #pragma unroll
     for (int v = 0; v < nv; ++v) dst[v] = __ldg(c.xcol + (off + v * c.ld));
     dst[nv] = __ldg(c.bcol + off);
@@ -449,7 +449,7 @@ __device__ __forceinline__ void zero_state(RowState<N> &S)
 
 // One warp marches its strip (30 columns) over the rows of segment seg: the whole stage for those
 // cells.  smax / flag accumulate the wave speed and status of the cells the lane finishes (stage 2).
-template <int N, int STAGE, bool IMP = false>
+template <int N, int STAGE, bool IMP = false, bool PEEL = true>
 __device__ __forceinline__ void march_strip(const StageArgs<float> &a, int strip, int seg, int lane, float dt,
                                             float &smax, unsigned &flag)
 {
@@ -473,19 +473,28 @@ __device__ __forceinline__ void march_strip(const StageArgs<float> &a, int strip
     zero_state<N>(B);
     float nxt[nv + 1];
     load_row<N, STAGE>(a, c, r0 - 1, nxt);
-    // rows r0 - 1 and r0 with the general flags, then pairs of rows strictly inside the segment
-    // without any test (one straight block per pair, so consecutive rows' independent work can
-    // overlap), then the last one or two rows with the general flags again.  Row r uses A as its
-    // current state when r - r0 is odd.
-    int r = r0 - 1;
-    row_body<N, STAGE, IMP>(a, c, r, r0, r1, dt, nxt, B, A, smax, flag);
-    row_body<N, STAGE, IMP>(a, c, r + 1, r0, r1, dt, nxt, A, B, smax, flag);
-    for (r = r0 + 1; r + 1 < r1; r += 2) {
-        row_body<N, STAGE, IMP, true>(a, c, r, r0, r1, dt, nxt, B, A, smax, flag);
-        row_body<N, STAGE, IMP, true>(a, c, r + 1, r0, r1, dt, nxt, A, B, smax, flag);
+    if constexpr (PEEL) {
+        // pairs of rows with the general flags at both ends of the segment (rows r0 - 1 and r0, then
+        // the last one or two), pairs strictly inside it without any test (one straight block per
+        // pair, so consecutive rows' independent work can overlap).  Row r uses A as its current state
+        // when r - r0 is odd.
+        int r = r0 - 1;
+        while (true) {
+            row_body<N, STAGE, IMP>(a, c, r, r0, r1, dt, nxt, B, A, smax, flag);
+            if (r + 1 <= r1) row_body<N, STAGE, IMP>(a, c, r + 1, r0, r1, dt, nxt, A, B, smax, flag);
+            r += 2;
+            if (r > r1) break;
+            for (; r + 1 < r1; r += 2) {
+                row_body<N, STAGE, IMP, true>(a, c, r, r0, r1, dt, nxt, B, A, smax, flag);
+                row_body<N, STAGE, IMP, true>(a, c, r + 1, r0, r1, dt, nxt, A, B, smax, flag);
+            }
+        }
+    } else {
+        for (int r = r0 - 1; r <= r1; r += 2) {
+            row_body<N, STAGE, IMP>(a, c, r, r0, r1, dt, nxt, B, A, smax, flag);
+            if (r + 1 <= r1) row_body<N, STAGE, IMP>(a, c, r + 1, r0, r1, dt, nxt, A, B, smax, flag);
+        }
     }
-    if (r <= r1) row_body<N, STAGE, IMP>(a, c, r, r0, r1, dt, nxt, B, A, smax, flag);
-    if (r + 1 <= r1) row_body<N, STAGE, IMP>(a, c, r + 1, r0, r1, dt, nxt, A, B, smax, flag);
 }
 
 }  // namespace zoomy

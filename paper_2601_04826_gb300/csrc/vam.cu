@@ -67,7 +67,7 @@ __device__ __forceinline__ double vq(const VamArgs &a, const double *Q, int v, i
     // state with mirrored ghosts; walls change the sign of the horizontal momenta (v = 1, 2)
     if (j < 0) return (v == 1 || v == 2) && a.bcl == 1 ? -Q[v * a.ld] : Q[v * a.ld];
     if (j >= a.nc) return (v == 1 || v == 2) && a.bcr == 1 ? -Q[v * a.ld + a.nc - 1] : Q[v * a.ld + a.nc - 1];
-    return Q[v * a.ld + j];
+    return Q[v * a.ld + bounds_idx(j, a.nc, &a.ctl->status)];
 }
 
 // b_x of cell j (0 <= j < nc): central difference with copied bed ghosts
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(128) k_vam_pcr(VamArgs a, int64_t N, int64_t s
         A = 0.0;
         C = 0.0;
         if (I - s >= 0) {
-            const double *Ym = Yin + (I - s) * YS;
+            const double *Ym = Yin + bounds_idx(I - s, N, &a.ctl->status) * YS;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 D -= arow[k] * Ym[16 + 4 * k + c];
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(128) k_vam_pcr(VamArgs a, int64_t N, int64_t s
             }
         }
         if (I + s < N) {
-            const double *Yp = Yin + (I + s) * YS;
+            const double *Yp = Yin + bounds_idx(I + s, N, &a.ctl->status) * YS;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 D -= crow[k] * Yp[4 * k + c];

@@ -312,6 +312,7 @@ zoomy_status zoomy::read_status(zoomy_ctx *c, double *t_total)
     if (h.status & DEV_NEGDEPTH) return set_error(ZOOMY_ENEGDEPTH, "a step produced a negative depth");
     if (h.status & DEV_NOWAVE) return set_error(ZOOMY_ECFL, "no positive finite wave speed for the CFL step");
     if (h.status & DEV_TIMEOUT) return set_error(ZOOMY_ETIMEOUT, "a device-side wait exceeded its limit");
+    if (h.status & DEV_BOUNDS) return set_error(ZOOMY_EBOUNDS, "a gather index fell outside its buffer");
     return ZOOMY_OK;
 }
 

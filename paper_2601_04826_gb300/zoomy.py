@@ -12,10 +12,12 @@ import os
 import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libzoomy.so")
+# ZOOMY_LIBRARY may name another build of the same sources (the bounds-checking libzoomy_debug.so)
+LIB_PATH = os.environ.get("ZOOMY_LIBRARY") or os.path.join(HERE, "libzoomy.so")
 
-ZOOMY_OK, ZOOMY_EINVAL, ZOOMY_ENOMEM, ZOOMY_ECUDA, ZOOMY_ENAN, ZOOMY_ENEGDEPTH, ZOOMY_ECFL, ZOOMY_ETIMEOUT, ZOOMY_ESTATE = range(9)
-STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENAN", "ENEGDEPTH", "ECFL", "ETIMEOUT", "ESTATE"]
+(ZOOMY_OK, ZOOMY_EINVAL, ZOOMY_ENOMEM, ZOOMY_ECUDA, ZOOMY_ENAN, ZOOMY_ENEGDEPTH, ZOOMY_ECFL, ZOOMY_ETIMEOUT, ZOOMY_ESTATE,
+ ZOOMY_EBOUNDS) = range(10)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENAN", "ENEGDEPTH", "ECFL", "ETIMEOUT", "ESTATE", "EBOUNDS"]
 MESH_1D, MESH_2D, MESH_TRI = 0, 1, 2
 BC_TRANSMISSIVE, BC_WALL = 0, 1
 FRICTION_NONE, FRICTION_SLIP_NEWTONIAN, FRICTION_MANNING = 0, 1, 2
