@@ -173,8 +173,13 @@ __device__ __forceinline__ void phase_loop(const EnsArgs &e, int phase, int k, i
     }
 }
 
+// One-warp CTAs: at level 1 (the ensemble workload) the kernel is held to 128 registers, 16 warps per
+// SM (its natural allocation, 152 registers, leaves 13); other levels take what they need.
 template <int N>
-__global__ void __launch_bounds__(32) k_ensemble_persistent(EnsArgs e)
+constexpr int ENS_MIN_CTAS = N == 1 ? 16 : 1;
+
+template <int N>
+__global__ void __launch_bounds__(32, ENS_MIN_CTAS<N>) k_ensemble_persistent(EnsArgs e)
 {
     phase_loop<N>(e, 0, 0, 0);
     if (!grid_barrier(e)) return;
@@ -187,7 +192,7 @@ __global__ void __launch_bounds__(32) k_ensemble_persistent(EnsArgs e)
 }
 
 template <int N>
-__global__ void __launch_bounds__(32) k_ensemble_phase(EnsArgs e, int phase, int k)
+__global__ void __launch_bounds__(32, ENS_MIN_CTAS<N>) k_ensemble_phase(EnsArgs e, int phase, int k)
 {
     run_item<N>(e, blockIdx.x, phase, k, threadIdx.x);
 }

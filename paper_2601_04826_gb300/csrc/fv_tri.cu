@@ -224,6 +224,7 @@ __global__ void __launch_bounds__(128) k_stage_tri(TriArgs a)
 {
     constexpr int m = N + 1, nv = 3 + 2 * N;
     const StageArgs<float> &s = a.s;
+    pdl_enter();  // the previous kernel's results (state, wave-speed slot, status) first
     if (*(volatile unsigned int *)&s.ctl->status) return;
     float dt;
     if (!step_dt(s, dt)) {
@@ -346,11 +347,8 @@ static cudaError_t launch_tri(const TriArgs &a, int stage, cudaStream_t st)
     int64_t blocks = (a.nc + 127) / 128;
     if (blocks > (int64_t)a.nsm * 16) blocks = (int64_t)a.nsm * 16;
     dim3 grid((unsigned)(blocks > 0 ? blocks : 1)), block(128);
-    if (stage == 1)
-        k_stage_tri<N, 1><<<grid, block, 0, st>>>(a);
-    else
-        k_stage_tri<N, 2><<<grid, block, 0, st>>>(a);
-    return cudaGetLastError();
+    // programmatic dependent launch: the launch and CTA ramp overlap the previous kernel's tail
+    return stage == 1 ? launch_pdl(k_stage_tri<N, 1>, grid, block, st, a) : launch_pdl(k_stage_tri<N, 2>, grid, block, st, a);
 }
 
 static cudaError_t launch_tri_level(int level, const TriArgs &a, int stage, cudaStream_t st)
