@@ -517,37 +517,52 @@ def run_closure(args):
             "gpu_launches": int(cl_["launches"]), "clocks": clk.summary()}
 
 
-def run_dambreak1d(args):
-    """The 1D dam break (2000 cells, level 1, FP64, slip + Newtonian, transmissive): a latency-bound
-    case (the whole state is 48 KB), reported as time per step.  Prints its own JSON line."""
+def _dambreak1d_time(zoomy, Q0, nx, level, steps, warmup, mode, wpc):
+    """us per step of one zoomy_step call of `steps` CFL steps (after `warmup` steps) in launch shape
+    (mode, warps per CTA); returns (us, simulated time advanced)."""
     import torch
 
-    from paper_2601_04826_gb300 import build, inputs, zoomy
-
-    build.build()
-    nx, level = 2000, 1
-    Q0 = inputs.dambreak_1d(nx, 0.0, 10.0, h_left=2.0, h_right=1.0, x_dam=5.0, level=level)
     ctx = zoomy.Context(zoomy.mesh_1d(nx, 0.0, 10.0, bc=(0, 0)), level,
                         zoomy.friction(zoomy.FRICTION_SLIP_NEWTONIAN, C=0.1, nu=0.01), cfl=0.45, dtype=zoomy.FP64)
+    ctx.tune_1d(mode, wpc)
     Q = torch.tensor(Q0, dtype=torch.float64, device="cuda")
-    ctx.step(Q, nsteps=args.warmup, dt=0.0)
+    ctx.step(Q, nsteps=warmup, dt=0.0)
     Q.copy_(torch.tensor(Q0, dtype=torch.float64))
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    ctx.step(Q, nsteps=args.steps, dt=0.0, sync=False)
+    ctx.step(Q, nsteps=steps, dt=0.0, sync=False)
     e1.record(stream)
     torch.cuda.synchronize()
     t = zoomy.zoomy_sync(ctx.ctx)
     ms = e0.elapsed_time(e1)
     ctx.close()
-    return {"metric": "time per SSP-RK2 step", "value": 1e3 * ms / args.steps, "unit": "us/step",
-            "cell_updates_per_s": nx * args.steps / (ms * 1e-3), "n_gpus": 1, "steps": args.steps,
+    return 1e3 * ms / steps, t
+
+
+def run_dambreak1d(args):
+    """The 1D dam break (2000 cells, level 1, FP64, slip + Newtonian, transmissive): a latency-bound
+    case (the whole state is 48 KB), reported as time per step in the automatic launch shape (two
+    launches per step, one-warp CTAs), with other launch shapes (zoomy_tune_1d) timed beside it.
+    Prints its own JSON line."""
+    from paper_2601_04826_gb300 import build, inputs, zoomy
+
+    build.build()
+    nx, level = 2000, 1
+    Q0 = inputs.dambreak_1d(nx, 0.0, 10.0, h_left=2.0, h_right=1.0, x_dam=5.0, level=level)
+    us, t = _dambreak1d_time(zoomy, Q0, nx, level, args.steps, args.warmup, zoomy.LAUNCH_AUTO, 0)
+    shapes = {}
+    for name, mode, wpc in [("per_stage_1warp", zoomy.LAUNCH_PER_STAGE, 1), ("per_stage_2warps", zoomy.LAUNCH_PER_STAGE, 2),
+                            ("persistent_1warp", zoomy.LAUNCH_PERSISTENT, 1)]:
+        shapes[name] = round(_dambreak1d_time(zoomy, Q0, nx, level, args.steps, args.warmup, mode, wpc)[0], 3)
+    return {"metric": "time per SSP-RK2 step", "value": us, "unit": "us/step",
+            "cell_updates_per_s": nx * 1e6 / us, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "1D shallow-moment level 1 dam break, 2000 cells on [0,10], h = 2 / 1, slip "
                                    "C=0.1 + Newtonian nu=0.01, transmissive, adaptive CFL 0.45",
                        "sim_time_advanced": t},
+            "launch_shapes_us_per_step": shapes,
             "gpu_launches": 2 * args.steps + 1}
 
 

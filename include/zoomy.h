@@ -203,6 +203,17 @@ zoomy_status zoomy_mass(zoomy_ctx *ctx, const void *Q, int64_t ld, double *out);
  * within [8, 64] rows. */
 zoomy_status zoomy_tune_set(zoomy_ctx *ctx, int32_t rows_per_warp, int32_t warps_per_block);
 
+/* Launch shape of the first-order 1D line (a performance knob; the state is bitwise the same for every
+ * setting).  The 1D kernels run one warp per 31 cells, each lane evaluating one face.  mode:
+ * ZOOMY_LAUNCH_AUTO (0) and ZOOMY_LAUNCH_PER_STAGE (1): two kernel launches per SSP-RK2 step (with
+ * programmatic dependent launch); ZOOMY_LAUNCH_PERSISTENT (2): all steps of a zoomy_step call in one
+ * cooperative launch whose CTAs meet at a grid barrier after each stage (taken where every CTA of the
+ * line can be resident at once and stage profiling is off; otherwise the call falls back to two launches
+ * per step).  warps_per_cta: 0 = automatic (1 below 65536 cells, else 8), or 1..8.  EINVAL for other
+ * values. */
+enum { ZOOMY_LAUNCH_AUTO = 0, ZOOMY_LAUNCH_PER_STAGE = 1, ZOOMY_LAUNCH_PERSISTENT = 2 };
+zoomy_status zoomy_tune_1d(zoomy_ctx *ctx, int32_t mode, int32_t warps_per_cta);
+
 /* Autotuner of the structured 2D decomposition: times both stage kernels on the state Q (device,
  * left unchanged; a temporary copy is used for the in-place stage) for each candidate rows_per_warp
  * (and warps_per_block where the kernel has that freedom) and keeps the fastest pair in the context.

@@ -12,13 +12,15 @@ namespace zoomy {
 struct DevCtl {
     unsigned int smax_f[2];          // max wave speed, FP32 bit pattern (s >= 0 orders like uint)
     unsigned long long smax_d[2];    // max wave speed, FP64 bit pattern
+    unsigned int bar[4];             // grid barrier of the persistent 1D launch (arrivals, generation, status)
     double t;                        // time advanced by the steps of the current call
     double dt_last;                  // last step size
     unsigned int status;             // DEV_* flags, sticky until the host clears them
     unsigned int pad;
 };
 
-enum : unsigned int { DEV_NAN = 1u, DEV_NEGDEPTH = 2u, DEV_NOWAVE = 4u, DEV_BOUNDS = 16u };
+// DEV_TIMEOUT: a device-side wait gave up (grid barriers, tensor-core completion waits)
+enum : unsigned int { DEV_NAN = 1u, DEV_NEGDEPTH = 2u, DEV_NOWAVE = 4u, DEV_TIMEOUT = 8u, DEV_BOUNDS = 16u };
 
 // Bounds-checking build (compiled with -DZOOMY_BOUNDS_CHECK, build(debug=True)): every gather index
 // of the stage, lifting and VAM kernels passes through bounds_idx before its access.  An index
@@ -76,7 +78,7 @@ struct StageArgs {
 // Step size of the current step: fixed, or dt = CFL * min Delta / max s (reading of the
 // adaptive time stepping with CFL = 0.45 of Sec. 3.1), s_max taken over Q^n.
 template <typename T>
-__device__ __forceinline__ bool step_dt(const StageArgs<T> &a, T &dt)
+__device__ __forceinline__ bool step_dt(const StageArgs<T> &a, int slot_in, T &dt)
 {
     if (a.dt_fixed > 0.0) {
         dt = T(a.dt_fixed);
@@ -84,24 +86,36 @@ __device__ __forceinline__ bool step_dt(const StageArgs<T> &a, T &dt)
     }
     double smax;
     if constexpr (sizeof(T) == 4)
-        smax = (double)__uint_as_float(*(volatile unsigned int *)&a.ctl->smax_f[a.slot_in]);
+        smax = (double)__uint_as_float(*(volatile unsigned int *)&a.ctl->smax_f[slot_in]);
     else
-        smax = __longlong_as_double((long long)*(volatile unsigned long long *)&a.ctl->smax_d[a.slot_in]);
+        smax = __longlong_as_double((long long)*(volatile unsigned long long *)&a.ctl->smax_d[slot_in]);
     if (!(smax > 0.0) || !(smax < 1e300)) return false;
     dt = T(a.cfl * a.dmin / smax);
     return true;
 }
 
+template <typename T>
+__device__ __forceinline__ bool step_dt(const StageArgs<T> &a, T &dt)
+{
+    return step_dt(a, a.slot_in, dt);
+}
+
 // Bookkeeping done once per step by one thread of the first stage.
 template <typename T>
-__device__ __forceinline__ void step_bookkeeping(const StageArgs<T> &a, T dt)
+__device__ __forceinline__ void step_bookkeeping(const StageArgs<T> &a, int slot_out, T dt)
 {
     a.ctl->t += (double)dt;
     a.ctl->dt_last = (double)dt;
     if constexpr (sizeof(T) == 4)
-        a.ctl->smax_f[a.slot_out] = 0u;
+        a.ctl->smax_f[slot_out] = 0u;
     else
-        a.ctl->smax_d[a.slot_out] = 0ull;
+        a.ctl->smax_d[slot_out] = 0ull;
+}
+
+template <typename T>
+__device__ __forceinline__ void step_bookkeeping(const StageArgs<T> &a, T dt)
+{
+    step_bookkeeping(a, a.slot_out, dt);
 }
 
 // Programmatic dependent launch: a kernel launched with launch_pdl waits here for its predecessor on

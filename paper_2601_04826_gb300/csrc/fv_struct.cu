@@ -15,20 +15,27 @@
 namespace zoomy {
 
 // ----------------------------------------------------------------------------------------
-// 1D: one thread per cell; the thread evaluates its two faces (cell-centric).
+// 1D: face-centric warps.  Lane l of a warp takes the face (c-1 | c), c = base + l, and lanes 0..30
+// update the cells base..base+30 (31 cells per warp) with their own face on the left and the next
+// lane's face on the right.  Each face is evaluated once (twice at warp seams) instead of once for
+// each of its two cells: the FP64 line is bound by the instruction stream of each warp.
 // ----------------------------------------------------------------------------------------
 
+constexpr int CELLS_PER_WARP_1D = 31;
+
+// Loads of the state go through L2 only (ld.global.cg) in every 1D kernel: the persistent kernel reads
+// data other CTAs of the same launch wrote before a grid barrier, which L1 may hold stale.
 template <int N, typename T>
-__device__ __forceinline__ void load_cell_1d(const StageArgs<T> &a, int i, CellRec<N, 1, T> &r, T *raw)
+__device__ __forceinline__ void load_cell_1d(const StageArgs<T> &a, const T *X, int i, CellRec<N, 1, T> &r, T *raw)
 {
     constexpr int m = N + 1;
     const int src = (int)bounds_idx(i < 0 ? 0 : (i >= a.nx ? a.nx - 1 : i), a.nx, &a.ctl->status);
     bool wall = (i < 0 && a.bc[0] == 1) || (i >= a.nx && a.bc[1] == 1);
-    T h = a.X[src];
+    T h = __ldcg(X + src);
     T ha[m];
 #pragma unroll
     for (int k = 0; k < m; ++k) {
-        ha[k] = a.X[(int64_t)(1 + k) * a.ld + src];
+        ha[k] = __ldcg(X + (int64_t)(1 + k) * a.ld + src);
         if (wall) ha[k] = -ha[k];
     }
     T b = a.bed ? a.bed[src] : T(0);
@@ -40,40 +47,44 @@ __device__ __forceinline__ void load_cell_1d(const StageArgs<T> &a, int i, CellR
     }
 }
 
+// One stage of the 31 cells base.. of a 1D line, called by all 32 lanes of a warp (the shuffles need the
+// full warp): each lane evaluates its face, then the lanes with a cell c < nx add both faces, the
+// source and the bottom stress, (stage 2) take the SSP-RK2 average with Q^n, write the cell to out
+// and return (stage 2) its wave speed.  Faces beyond the line (c > nx) read clamped cells and are not
+// used.  Kept out of line: the per-stage kernels and the persistent kernel call this one compiled body,
+// so both launch shapes execute the same instructions (inlined into different kernels, the compiler
+// may contract multiplies and adds into FMAs differently, which changes the last bit).
 template <int N, typename T, int STAGE>
-__global__ void __launch_bounds__(256) k_stage_1d(StageArgs<T> a)
+__device__ __noinline__ T stage_1d_warp(const StageArgs<T> &a, const T *X, const T *Qn, T *out, T dt, int base)
 {
     constexpr int m = N + 1, nv = 1 + m;
-    pdl_enter();
-    if (*(volatile unsigned int *)&a.ctl->status) return;
-    T dt;
-    if (!step_dt(a, dt)) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.ctl->status, DEV_NOWAVE);
-        return;
+    const int lane = threadIdx.x & 31, c = base + lane;
+    CellRec<N, 1, T> cl, cc;
+    T raw[nv];
+    load_cell_1d<N, T>(a, X, c - 1, cl, nullptr);
+    load_cell_1d<N, T>(a, X, c, cc, raw);
+    T fl[nv], nl[nv], pl;
+    face_term<N, 1, T>(cl, frame<N, 1, T, false>(cl), cc, frame<N, 1, T, false>(cc), a.g, a.hdry, fl, pl, nl);
+    // the right face (c | c+1) is the next lane's
+    T fr[nv], nr[nv];
+#pragma unroll
+    for (int v = 0; v < nv; ++v) {
+        fr[v] = __shfl_down_sync(0xffffffffu, fl[v], 1);
+        nr[v] = __shfl_down_sync(0xffffffffu, nl[v], 1);
     }
-    if (STAGE == 1 && blockIdx.x == 0 && threadIdx.x == 0) step_bookkeeping(a, dt);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const T pr = __shfl_down_sync(0xffffffffu, pl, 1);
     T s = T(0);
-    if (i < a.nx) {
-        CellRec<N, 1, T> cl, cc, cr;
-        T raw[nv];
-        load_cell_1d<N, T>(a, i - 1, cl, nullptr);
-        load_cell_1d<N, T>(a, i, cc, raw);
-        load_cell_1d<N, T>(a, i + 1, cr, nullptr);
+    if (lane < CELLS_PER_WARP_1D && c < a.nx) {
         T acc[nv];
 #pragma unroll
         for (int v = 0; v < nv; ++v) acc[v] = T(0);
-        T fc[nv], nc[nv], pd;
-        // left face (i-1 | i): this cell is R
-        face_term<N, 1, T>(cl, frame<N, 1, T, false>(cl), cc, frame<N, 1, T, false>(cc), a.g, a.hdry, fc, pd, nc);
+        // left face: this cell is R; right face: this cell is L
 #pragma unroll
-        for (int v = 0; v < nv; ++v) acc[v] += fc[v] - nc[v];
-        acc[1] -= pd;
-        // right face (i | i+1): this cell is L
-        face_term<N, 1, T>(cc, frame<N, 1, T, false>(cc), cr, frame<N, 1, T, false>(cr), a.g, a.hdry, fc, pd, nc);
+        for (int v = 0; v < nv; ++v) acc[v] += fl[v] - nl[v];
+        acc[1] -= pl;
 #pragma unroll
-        for (int v = 0; v < nv; ++v) acc[v] -= fc[v] + nc[v];
-        acc[1] -= pd;
+        for (int v = 0; v < nv; ++v) acc[v] -= fr[v] + nr[v];
+        acc[1] -= pr;
         T sa[m];
         newtonian<N, 1, T>(cc, a.nu_rho, sa, nullptr);
         T y[nv];
@@ -86,7 +97,7 @@ __global__ void __launch_bounds__(256) k_stage_1d(StageArgs<T> a)
             bottom_friction<N, 1, T>(y[0], y + 1, nullptr, a.fric, a.C_rho, a.gn2, dt, a.hdry);
         if (STAGE == 2) {
 #pragma unroll
-            for (int v = 0; v < nv; ++v) y[v] = T(0.5) * (a.Qn[(int64_t)v * a.ld + i] + y[v]);
+            for (int v = 0; v < nv; ++v) y[v] = T(0.5) * (__ldcg(Qn + (int64_t)v * a.ld + c) + y[v]);
             CellRec<N, 1, T> co;
             make_cell<N, 1, T>(co, y[0], T(0), y + 1, nullptr, a.hdry);
             s = wavespeed<N, 1, T>(co, a.g);
@@ -96,9 +107,94 @@ __global__ void __launch_bounds__(256) k_stage_1d(StageArgs<T> a)
             if (flag) atomicOr(&a.ctl->status, flag);
         }
 #pragma unroll
-        for (int v = 0; v < nv; ++v) a.out[(int64_t)v * a.ld + i] = y[v];
+        for (int v = 0; v < nv; ++v) out[(int64_t)v * a.ld + c] = y[v];
     }
+    return s;
+}
+
+// One stage, one warp per 31 cells (warp-uniform exit past the line).
+template <int N, typename T, int STAGE>
+__global__ void __launch_bounds__(256) k_stage_1d(const __grid_constant__ StageArgs<T> a)
+{
+    pdl_enter();
+    if (*(volatile unsigned int *)&a.ctl->status) return;
+    T dt;
+    if (!step_dt(a, a.slot_in, dt)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.ctl->status, DEV_NOWAVE);
+        return;
+    }
+    if (STAGE == 1 && blockIdx.x == 0 && threadIdx.x == 0) step_bookkeeping(a, a.slot_out, dt);
+    const int base = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * CELLS_PER_WARP_1D;
+    if (base >= a.nx) return;
+    const T s = stage_1d_warp<N, T, STAGE>(a, a.X, a.Qn, a.out, dt, base);
     if (STAGE == 2) reduce_smax<T>(a.ctl, a.slot_out, s);
+}
+
+// Grid barrier of a cooperative launch on bar = DevCtl::bar (arrivals, generation, status snapshot;
+// zero at the launch).  Thread 0 of each CTA arrives; the last one copies the sticky status into the
+// snapshot before it releases the others, so every CTA takes the same decision.  Returns true when the
+// CTA is to stop: the snapshot shows a device-detected error (the per-stage kernels skip their work
+// then too), or this CTA's bounded wait ran out (DEV_TIMEOUT).
+__device__ __forceinline__ bool grid_barrier_1d(unsigned *bar, unsigned nbar, unsigned *status, long long spin_limit)
+{
+    __shared__ unsigned stop;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vb = bar;
+        const unsigned g0 = vb[1];
+        __threadfence();
+        if (atomicAdd(bar, 1u) == nbar - 1) {
+            vb[0] = 0u;
+            vb[2] = *(volatile unsigned *)status;
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long it = 0;
+            while (vb[1] == g0) {
+                if (++it > spin_limit) {
+                    atomicOr(status, DEV_TIMEOUT);
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        stop = vb[1] == g0 || vb[2] != 0u;
+    }
+    __syncthreads();
+    return stop != 0u;
+}
+
+// Every step of a zoomy_step call on a short 1D line in one cooperative launch: stage 1 (Q -> Q1),
+// grid barrier, stage 2 (Q1 and Q^n = Q -> Q, wave-speed maximum), grid barrier.  The stages are the
+// per-stage kernels' warp body (stage_1d_warp, the same compiled function); the step size, the time
+// and wave-speed slot bookkeeping and the skip after a device-detected error are those of two
+// launches per step, so the state is bitwise the same.
+template <int N, typename T>
+__global__ void __launch_bounds__(256) k_steps_1d(const __grid_constant__ StageArgs<T> a, T *Q, T *Q1, int nsteps,
+                                                  unsigned nbar, long long spin_limit)
+{
+    const int base = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * CELLS_PER_WARP_1D;
+    unsigned *bar = a.ctl->bar;
+    // an error left by an earlier call of this context skips the call (as in the per-stage kernels);
+    // taken from the barrier's snapshot so that every CTA decides alike
+    if (grid_barrier_1d(bar, nbar, &a.ctl->status, spin_limit)) return;
+    for (int k = 0; k < nsteps; ++k) {
+        const int slot_in = k & 1, slot_out = (k + 1) & 1;
+        T dt;
+        // every CTA reads the same s_max (final before the last barrier), so all of them stop here
+        if (!step_dt(a, slot_in, dt)) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.ctl->status, DEV_NOWAVE);
+            return;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) step_bookkeeping(a, slot_out, dt);
+        T s = T(0);
+        if (base < a.nx) stage_1d_warp<N, T, 1>(a, Q, Q, Q1, dt, base);
+        if (grid_barrier_1d(bar, nbar, &a.ctl->status, spin_limit)) return;
+        if (base < a.nx) s = stage_1d_warp<N, T, 2>(a, Q1, Q, Q, dt, base);
+        reduce_smax<T>(a.ctl, slot_out, s);
+        if (grid_barrier_1d(bar, nbar, &a.ctl->status, spin_limit)) return;
+    }
 }
 
 // ----------------------------------------------------------------------------------------
@@ -292,13 +388,11 @@ __global__ void __launch_bounds__(128) k_stage_2d(StageArgs<T> a)
 // ----------------------------------------------------------------------------------------
 
 template <int N, typename T>
-static cudaError_t launch_1d(const StageArgs<T> &a, int stage, cudaStream_t st)
+static cudaError_t launch_1d(const StageArgs<T> &a, int stage, int warps_per_cta, cudaStream_t st)
 {
-    // small lines (the work is FP64-rate bound, not memory bound): one-warp CTAs spread the cells
-    // over as many SMs as possible; large lines use 256-thread CTAs
-    // (programmatic dependent launch: each stage's launch overlaps the previous kernel's tail)
-    const int bs = a.nx < 65536 ? 32 : 256;
-    dim3 grid((a.nx + bs - 1) / bs), block(bs);
+    // programmatic dependent launch: each stage's launch overlaps the previous kernel's tail
+    const int nwarps = (a.nx + CELLS_PER_WARP_1D - 1) / CELLS_PER_WARP_1D;
+    dim3 grid((nwarps + warps_per_cta - 1) / warps_per_cta), block(32 * warps_per_cta);
     if (stage == 1) return launch_pdl(k_stage_1d<N, T, 1>, grid, block, st, a);
     return launch_pdl(k_stage_1d<N, T, 2>, grid, block, st, a);
 }
@@ -316,28 +410,65 @@ static cudaError_t launch_2d(const StageArgs<T> &a, int stage, int warps_per_blo
 }
 
 template <typename T>
-cudaError_t launch_stage_struct(int dim, int level, const StageArgs<T> &a, int stage, int warps_per_block,
+cudaError_t launch_stage_struct(int dim, int level, const StageArgs<T> &a, int stage, int block_shape,
                                 cudaStream_t st)
 {
     if (dim == 1) {
+        const int warps_per_cta = block_shape;
         switch (level) {
-            case 0: return launch_1d<0, T>(a, stage, st);
-            case 1: return launch_1d<1, T>(a, stage, st);
-            case 2: return launch_1d<2, T>(a, stage, st);
-            case 3: return launch_1d<3, T>(a, stage, st);
-            case 4: return launch_1d<4, T>(a, stage, st);
+            case 0: return launch_1d<0, T>(a, stage, warps_per_cta, st);
+            case 1: return launch_1d<1, T>(a, stage, warps_per_cta, st);
+            case 2: return launch_1d<2, T>(a, stage, warps_per_cta, st);
+            case 3: return launch_1d<3, T>(a, stage, warps_per_cta, st);
+            case 4: return launch_1d<4, T>(a, stage, warps_per_cta, st);
         }
     } else {
         switch (level) {
-            case 0: return launch_2d<0, T>(a, stage, warps_per_block, st);
-            case 1: return launch_2d<1, T>(a, stage, warps_per_block, st);
-            case 2: return launch_2d<2, T>(a, stage, warps_per_block, st);
-            case 3: return launch_2d<3, T>(a, stage, warps_per_block, st);
-            case 4: return launch_2d<4, T>(a, stage, warps_per_block, st);
+            case 0: return launch_2d<0, T>(a, stage, block_shape, st);
+            case 1: return launch_2d<1, T>(a, stage, block_shape, st);
+            case 2: return launch_2d<2, T>(a, stage, block_shape, st);
+            case 3: return launch_2d<3, T>(a, stage, block_shape, st);
+            case 4: return launch_2d<4, T>(a, stage, block_shape, st);
         }
     }
     return cudaErrorInvalidValue;
 }
+
+template <int N, typename T>
+static cudaError_t launch_steps_1d_n(const StageArgs<T> &a, T *Q, T *Q1, int nsteps, int warps_per_cta, int nsm,
+                                     cudaStream_t st)
+{
+    const int nwarps = (a.nx + CELLS_PER_WARP_1D - 1) / CELLS_PER_WARP_1D;
+    const unsigned nb = (unsigned)((nwarps + warps_per_cta - 1) / warps_per_cta);
+    const int bs = 32 * warps_per_cta;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_steps_1d<N, T>, bs, 0);
+    if (e != cudaSuccess) return e;
+    if ((long long)nb > (long long)per_sm * nsm) return cudaErrorCooperativeLaunchTooLarge;
+    long long spin = 20000000LL;  // at least 0.6 s of 32 ns naps
+    void *args[] = {(void *)&a, (void *)&Q, (void *)&Q1, (void *)&nsteps, (void *)&nb, (void *)&spin};
+    return cudaLaunchCooperativeKernel((const void *)k_steps_1d<N, T>, dim3(nb), dim3(bs), args, 0, st);
+}
+
+template <typename T>
+cudaError_t launch_steps_1d(int level, const StageArgs<T> &a, T *Q, T *Q1, int nsteps, int warps_per_cta, int nsm,
+                            cudaStream_t st)
+{
+    if (warps_per_cta < 1 || warps_per_cta > 8) return cudaErrorInvalidValue;
+    switch (level) {
+        case 0: return launch_steps_1d_n<0, T>(a, Q, Q1, nsteps, warps_per_cta, nsm, st);
+        case 1: return launch_steps_1d_n<1, T>(a, Q, Q1, nsteps, warps_per_cta, nsm, st);
+        case 2: return launch_steps_1d_n<2, T>(a, Q, Q1, nsteps, warps_per_cta, nsm, st);
+        case 3: return launch_steps_1d_n<3, T>(a, Q, Q1, nsteps, warps_per_cta, nsm, st);
+        case 4: return launch_steps_1d_n<4, T>(a, Q, Q1, nsteps, warps_per_cta, nsm, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template cudaError_t launch_steps_1d<float>(int, const StageArgs<float> &, float *, float *, int, int, int,
+                                            cudaStream_t);
+template cudaError_t launch_steps_1d<double>(int, const StageArgs<double> &, double *, double *, int, int, int,
+                                             cudaStream_t);
 
 template cudaError_t launch_stage_struct<float>(int, int, const StageArgs<float> &, int, int, cudaStream_t);
 template cudaError_t launch_stage_struct<double>(int, int, const StageArgs<double> &, int, int, cudaStream_t);

@@ -249,6 +249,22 @@ static void fill_args(zoomy_ctx *c, StageArgs<T> &a, int64_t ld, double dt)
     a.nsegs = (int)((c->ny + a.H - 1) / a.H);
 }
 
+// Warps per CTA of the first-order 1D kernels (zoomy_tune_1d, else automatic: lines shorter than
+// 65536 cells spread one-warp CTAs over the SMs, longer ones use 8-warp CTAs).
+static int warps_per_cta_1d(const zoomy_ctx *c)
+{
+    if (c->warps_per_cta_1d > 0) return c->warps_per_cta_1d;
+    return c->nx < 65536 ? 1 : 8;
+}
+
+// The persistent 1D launch (first-order lines, stage profiling off) is taken only when zoomy_tune_1d
+// asks for it: two launches per step with programmatic dependent launch measured faster on GB300.
+static bool persistent_1d(const zoomy_ctx *c, int nsteps)
+{
+    if (c->dim != 1 || c->order != 1 || c->prof_on || nsteps < 1) return false;
+    return c->launch_1d == ZOOMY_LAUNCH_PERSISTENT;
+}
+
 template <typename T>
 static cudaError_t launch_stage(zoomy_ctx *c, const StageArgs<T> &a, int stage)
 {
@@ -258,7 +274,8 @@ static cudaError_t launch_stage(zoomy_ctx *c, const StageArgs<T> &a, int stage)
         if (c->dim == 2 && (int64_t)c->nv * a.ld < (1LL << 31))
             return launch_stage_2d_f32(c->level, a, stage, c->warps_per_block, c->stream);
     }
-    return launch_stage_struct<T>(c->dim, c->level, a, stage, c->warps_per_block, c->stream);
+    return launch_stage_struct<T>(c->dim, c->level, a, stage, c->dim == 1 ? warps_per_cta_1d(c) : c->warps_per_block,
+                                  c->stream);
 }
 
 template <typename T>
@@ -278,6 +295,12 @@ static zoomy_status run_steps(zoomy_ctx *c, T *Q, int64_t ld, double dt, int nst
     if (c->kind == ZOOMY_MESH_TRI) return tri_run_steps(c, (float *)Q, ld, dt, nsteps);
     StageArgs<T> a;
     fill_args<T>(c, a, ld, dt);
+    if (persistent_1d(c, nsteps)) {
+        // DevCtl::bar was zeroed with the wave-speed slots at the start of the call
+        cudaError_t e = launch_steps_1d<T>(c->level, a, Q, Q1, nsteps, warps_per_cta_1d(c), c->nsm, c->stream);
+        if (e == cudaSuccess) return ZOOMY_OK;
+        if (e != cudaErrorCooperativeLaunchTooLarge) return cuda_fail(e, "persistent 1D launch");
+    }
     for (int s = 0; s < nsteps; ++s) {
         a.slot_in = s & 1;
         a.slot_out = (s + 1) & 1;
@@ -466,6 +489,18 @@ extern "C" zoomy_status zoomy_tune_set(zoomy_ctx *c, int32_t rows_per_warp, int3
         return set_error(ZOOMY_EINVAL, "zoomy_tune_set: rows_per_warp in [1, 4096], warps_per_block in [1, 32]");
     c->rows_per_warp = rows_per_warp;
     c->warps_per_block = warps_per_block;
+    return ZOOMY_OK;
+}
+
+extern "C" zoomy_status zoomy_tune_1d(zoomy_ctx *c, int32_t mode, int32_t warps_per_cta)
+{
+    if (!c) return set_error(ZOOMY_EINVAL, "zoomy_tune_1d: NULL context");
+    if (mode < ZOOMY_LAUNCH_AUTO || mode > ZOOMY_LAUNCH_PERSISTENT)
+        return set_error(ZOOMY_EINVAL, "zoomy_tune_1d: mode must be 0, 1 or 2");
+    if (warps_per_cta < 0 || warps_per_cta > 8)
+        return set_error(ZOOMY_EINVAL, "zoomy_tune_1d: warps_per_cta must be in [0, 8]");
+    c->launch_1d = mode;
+    c->warps_per_cta_1d = warps_per_cta;
     return ZOOMY_OK;
 }
 

@@ -46,6 +46,7 @@ struct zoomy_ctx {
     double *partials = nullptr;
     // structured 2D decomposition (rows per warp segment, warps per block)
     int rows_per_warp = 0, warps_per_block = 4;  // rows_per_warp 0: rows_per_warp_for()
+    int launch_1d = 0, warps_per_cta_1d = 0;     // zoomy_tune_1d
     // stage-kernel profiling (zoomy_profile_enable)
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_events;  // pool, reused
@@ -68,10 +69,6 @@ struct zoomy_ctx {
 };
 
 namespace zoomy {
-// Status bit of a device-side wait that gave up (ensemble grid barrier, tensor-core completion
-// waits); the other bits (DEV_NAN, DEV_NEGDEPTH, DEV_NOWAVE) are in fv_common.cuh.
-enum : unsigned int { DEV_TIMEOUT = 8u };
-
 // Segment height of the structured 2D row-marching kernels when none was set: about
 // warps_per_sm warps per SM over the grid (30-column strips), within [8, 64] rows.
 inline int rows_per_warp_for(int64_t nx, int64_t ny, int nsm, int warps_per_sm)

@@ -22,6 +22,7 @@ MESH_1D, MESH_2D, MESH_TRI = 0, 1, 2
 BC_TRANSMISSIVE, BC_WALL = 0, 1
 FRICTION_NONE, FRICTION_SLIP_NEWTONIAN, FRICTION_MANNING = 0, 1, 2
 FP32, FP64 = 0, 1
+LAUNCH_AUTO, LAUNCH_PER_STAGE, LAUNCH_PERSISTENT = 0, 1, 2
 
 
 class ZoomyError(RuntimeError):
@@ -63,6 +64,7 @@ _SIGNATURES = [
     ("zoomy_max_wavespeed", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_double)]),
     ("zoomy_mass", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_double)]),
     ("zoomy_tune_set", C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
+    ("zoomy_tune_1d", C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
     ("zoomy_autotune", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_char_p, C.POINTER(C.c_int32),
                                  C.POINTER(C.c_double)]),
     ("zoomy_closure_set", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double]),
@@ -224,6 +226,10 @@ def zoomy_mass(ctx, Q, ld):
 
 def zoomy_tune_set(ctx, rows_per_warp, warps_per_block):
     _check(lib().zoomy_tune_set(ctx, rows_per_warp, warps_per_block))
+
+
+def zoomy_tune_1d(ctx, mode, warps_per_cta=0):
+    _check(lib().zoomy_tune_1d(ctx, mode, warps_per_cta))
 
 
 def zoomy_autotune(ctx, Q, ld, cache_path=None):
@@ -500,6 +506,10 @@ class Context:
 
     def tune(self, rows_per_warp, warps_per_block):
         zoomy_tune_set(self.ctx, rows_per_warp, warps_per_block)
+
+    def tune_1d(self, mode, warps_per_cta=0):
+        """Launch shape of a first-order 1D line (LAUNCH_AUTO / LAUNCH_PER_STAGE / LAUNCH_PERSISTENT)."""
+        zoomy_tune_1d(self.ctx, mode, warps_per_cta)
 
     def autotune(self, Q, cache_path=None):
         return zoomy_autotune(self.ctx, Q, self._ld(Q), cache_path)
