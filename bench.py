@@ -288,8 +288,7 @@ def run_ours(args, rank, world, local_rank):
 
 def run_tri(args):
     """Config-3 workload: ~4M-triangle jittered Delaunay mesh, level 3, Manning, circular dam break into a
-    dry domain, walls.  Times the automatic stage kernel (zoomy_tune_tri) and, in a shorter pass, the
-    other one beside it.  Prints its own JSON line (not the default bench line)."""
+    dry domain, walls.  Prints its own JSON line (not the default bench line)."""
     import numpy as np
     import torch
 
@@ -302,38 +301,23 @@ def run_tri(args):
     nc = len(tris)
     ctx = zoomy.Context(zoomy.mesh_tri(verts, tris, bc=1), level, zoomy.friction(2, manning_n=0.03), dtype=0)
     perm = ctx.permutation()
-    Q0p = np.ascontiguousarray(Q0[:, perm])
+    Q = torch.tensor(np.ascontiguousarray(Q0[:, perm]), dtype=torch.float32, device="cuda")
+    ctx.step(Q, nsteps=args.warmup, dt=0.0)
     stream = torch.cuda.current_stream()
-
-    def timed(variant, steps, clk=None):
-        ctx.tune_tri(variant)
-        Q = torch.tensor(Q0p, dtype=torch.float32, device="cuda")
-        ctx.step(Q, nsteps=args.warmup, dt=0.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
         torch.cuda.synchronize()
-        if clk:
-            clk.__enter__()
         e0.record(stream)
-        ctx.step(Q, nsteps=steps, dt=0.0, sync=False)
+        ctx.step(Q, nsteps=args.steps, dt=0.0, sync=False)
         e1.record(stream)
         torch.cuda.synchronize()
-        if clk:
-            clk.__exit__(None, None, None)
-        zoomy.zoomy_sync(ctx.ctx)
-        return e0.elapsed_time(e1), Q
-
-    clk = ClockSampler(0)
-    ms, Q = timed(args.tri_variant, args.steps, clk)
+    zoomy.zoomy_sync(ctx.ctx)
+    ms = e0.elapsed_time(e1)
     # per-kernel durations from a second pass with events around every launch (they end the
     # programmatic overlap of consecutive launches, so the timed pass runs without them)
     zoomy.zoomy_profile_enable(ctx.ctx, True)
     ctx.step(Q, nsteps=min(args.steps, 200), dt=0.0)
     launches, kms = zoomy.zoomy_profile_read(ctx.ctx)
-    zoomy.zoomy_profile_enable(ctx.ctx, False)
-    variants = {}
-    for name, v in (("cell_centric", zoomy.TRI_CELL), ("tiled_face_centric", zoomy.TRI_TILED)):
-        n = min(args.steps, 100)
-        variants[name] = round(timed(v, n)[0] / n, 4)
     ctx.close()
     hbm, peak_kind = peaks()
     # per cell: state nv, bed, geometry (3 neighbours int32 + 3 normals + 3 |e|/|Omega| as float32) read once,
@@ -342,21 +326,17 @@ def run_tri(args):
     b1, b2 = 4 * (nv + 1 + nv) + geo, 4 * (nv + 1 + nv + nv) + geo
     avg2 = kms[1] / max(launches[1], 1)
     ach = b2 * nc / (avg2 * 1e-3) / 1e9
-    tiled = args.tri_variant != zoomy.TRI_CELL
-    kernel = "k_stage_tri_tile<3,2>" if tiled else "k_stage_tri<3,2>"
     return {"metric": METRIC, "value": nc * args.steps / (ms * 1e-3), "unit": "cell-updates/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded jittered Delaunay)",
             "config": {"workload": "2D shallow-moment level 3 on a jittered-point Delaunay triangle mesh "
-                                   f"({nc} cells, Morton order), Manning n=0.03, dry outside a circular dam, walls",
-                       "stage_kernel": "tiled face-centric" if tiled else "cell-centric"},
-            "roofline": {"bound": "hbm", "kernel": kernel, "achieved": ach, "peak": hbm,
+                                   f"({nc} cells, Morton order), Manning n=0.03, dry outside a circular dam, walls"},
+            "roofline": {"bound": "hbm", "kernel": "k_stage_tri<3,2>", "achieved": ach, "peak": hbm,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / hbm,
                          "traffic": ncu_traffic(TRI_KERNEL_SOURCES) if args.tri_side == 1415 else None,
                          "algorithmic_bytes_per_launch": b2 * nc,
                          "avg_launch_ms": {"stage1": kms[0] / max(launches[0], 1), "stage2": avg2},
                          "launch_timing": "CUDA events around each launch in a second pass after the timed one"},
-            "variants_ms_per_step": variants,
             "gpu_launches": int(2 * args.steps + 1), "clocks": clk.summary()}
 
 
@@ -752,8 +732,6 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
-    ap.add_argument("--tri-variant", type=int, default=0, choices=[0, 1, 2],
-                    help="triangle stage kernel: 0 automatic, 1 cell-centric, 2 tiled face-centric")
     ap.add_argument("--workload", choices=["grid", "tri", "ensemble", "closure", "closure-kernels", "dambreak1d",
                                            "lift", "vam"],
                     default="grid",

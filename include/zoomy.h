@@ -214,13 +214,6 @@ zoomy_status zoomy_tune_set(zoomy_ctx *ctx, int32_t rows_per_warp, int32_t warps
 enum { ZOOMY_LAUNCH_AUTO = 0, ZOOMY_LAUNCH_PER_STAGE = 1, ZOOMY_LAUNCH_PERSISTENT = 2 };
 zoomy_status zoomy_tune_1d(zoomy_ctx *ctx, int32_t mode, int32_t warps_per_cta);
 
-/* Stage kernel of a triangle mesh (a performance knob; both match the oracle, their results differ in
- * rounding).  ZOOMY_TRI_AUTO (0) picks; ZOOMY_TRI_CELL (1): one thread per cell evaluating its three
- * faces (each face from both sides); ZOOMY_TRI_TILED (2): 128-cell tiles of the Morton order, each face
- * inside a tile evaluated once, cell records built once in shared memory.  EINVAL for other values. */
-enum { ZOOMY_TRI_AUTO = 0, ZOOMY_TRI_CELL = 1, ZOOMY_TRI_TILED = 2 };
-zoomy_status zoomy_tune_tri(zoomy_ctx *ctx, int32_t variant);
-
 /* Autotuner of the structured 2D decomposition: times both stage kernels on the state Q (device,
  * left unchanged; a temporary copy is used for the in-place stage) for each candidate rows_per_warp
  * (and warps_per_block where the kernel has that freedom) and keeps the fastest pair in the context.

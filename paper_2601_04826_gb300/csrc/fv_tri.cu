@@ -341,311 +341,6 @@ __global__ void __launch_bounds__(128) k_stage_tri(TriArgs a)
     }
 }
 
-// ------------------------------------------------------------------------------------------
-// Device: tiled face-centric stage kernel
-// ------------------------------------------------------------------------------------------
-//
-// A CTA takes a tile of TRI_TILE consecutive (Morton-ordered) cells.  Each cell's record (primitive
-// velocities, wave-speed parts and flux products) is built once, in the x/y frame, into shared
-// memory.  A face is evaluated once when both of its cells are in the tile (by the lower cell, which
-// writes both cells' contributions); a face to a cell outside the tile, or on the boundary, is
-// evaluated by its tile's cell only.  The face frame needs the record rotated into (n, t): with
-// alpha_n = alpha_x n_x + alpha_y n_y and alpha_t = alpha_y n_x - alpha_x n_y the flux products are
-// quadratic forms, so
-//   g_nn = g_xx n_x^2 + 2 g_xy n_x n_y + g_yy n_y^2,   g_nt = g_xy (n_x^2 - n_y^2) + (g_yy - g_xx) n_x n_y,
-// and |u|, sum |alpha_k|^2 and sum |alpha_k| are invariant.  The three face contributions of a cell
-// land in fixed slots and are added in face order: deterministic, no atomics.
-
-constexpr int TRI_TILE = 128;
-
-template <int N>
-struct TriTileSmem {
-    static constexpr int m = N + 1, nv = 3 + 2 * N, nrec = 5 + 5 * m;
-    float rec[nrec][TRI_TILE];           // h, b, |u|, s2, s1, alpha_x[m], alpha_y[m], g_xx[m], g_xy[m], g_yy[m]
-    float contrib[3][nv][TRI_TILE];      // face slot, variable, cell (x/y frame, times |e|/|Omega|)
-    float geo[9][TRI_TILE];              // n_x[3], n_y[3], |e|/|Omega| [3]
-    int32_t nbr[3][TRI_TILE];
-    int32_t fj[3 * TRI_TILE];            // face list: neighbour
-    uint16_t ftf[3 * TRI_TILE];          // face list: (tile cell << 2) | face
-    int wsum[TRI_TILE / 32];
-    float wmax[TRI_TILE / 32];
-};
-
-template <int N>
-__device__ __forceinline__ void tile_store_rec(TriTileSmem<N> &S, int t, const CellRec<N, 2, float> &r)
-{
-    constexpr int m = N + 1;
-    S.rec[0][t] = r.h;
-    S.rec[1][t] = r.b;
-    S.rec[2][t] = r.um;
-    S.rec[3][t] = r.s2;
-    S.rec[4][t] = r.s1;
-#pragma unroll
-    for (int k = 0; k < m; ++k) {
-        S.rec[5 + k][t] = r.a[k];
-        S.rec[5 + m + k][t] = r.c[k];
-        S.rec[5 + 2 * m + k][t] = r.gaa[k];
-        S.rec[5 + 3 * m + k][t] = r.gab[k];
-        S.rec[5 + 4 * m + k][t] = r.gbb[k];
-    }
-}
-
-// Record of x/y-frame values (h, b, |u|, s2, s1, alpha_x, alpha_y, g_xx, g_xy, g_yy) rotated into the
-// frame of normal (nx, ny); reflect: the wall ghost (normal moments and g_nt change sign).
-template <int N>
-__device__ __forceinline__ void tile_rotate(float h, float b, float um, float s2, float s1, const float *ax,
-                                            const float *ay, const float *gxx, const float *gxy, const float *gyy,
-                                            float nx, float ny, bool reflect, CellRec<N, 2, float> &r)
-{
-    constexpr int m = N + 1;
-    r.h = h;
-    r.b = b;
-    r.um = um;
-    r.s2 = s2;
-    r.s1 = s1;
-    const float nxx = nx * nx, nyy = ny * ny, nxy = nx * ny;
-#pragma unroll
-    for (int k = 0; k < m; ++k) {
-        const float an = fmaf(ax[k], nx, ay[k] * ny), at = fmaf(ay[k], nx, -ax[k] * ny);
-        const float gnn = fmaf(gxx[k], nxx, fmaf(2.0f * gxy[k], nxy, gyy[k] * nyy));
-        const float gnt = fmaf(gxy[k], nxx - nyy, (gyy[k] - gxx[k]) * nxy);
-        r.a[k] = reflect ? -an : an;
-        r.c[k] = at;
-        r.gaa[k] = gnn;
-        r.gab[k] = reflect ? -gnt : gnt;
-        r.gbb[k] = 0.0f;
-    }
-}
-
-template <int N>
-__device__ __forceinline__ void tile_rotate_smem(const TriTileSmem<N> &S, int t, float nx, float ny, bool reflect,
-                                                 CellRec<N, 2, float> &r)
-{
-    constexpr int m = N + 1;
-    float ax[m], ay[m], gxx[m], gxy[m], gyy[m];
-#pragma unroll
-    for (int k = 0; k < m; ++k) {
-        ax[k] = S.rec[5 + k][t];
-        ay[k] = S.rec[5 + m + k][t];
-        gxx[k] = S.rec[5 + 2 * m + k][t];
-        gxy[k] = S.rec[5 + 3 * m + k][t];
-        gyy[k] = S.rec[5 + 4 * m + k][t];
-    }
-    tile_rotate<N>(S.rec[0][t], S.rec[1][t], S.rec[2][t], S.rec[3][t], S.rec[4][t], ax, ay, gxx, gxy, gyy, nx, ny,
-                   reflect, r);
-}
-
-template <int N>
-__device__ __forceinline__ void tile_make_xy(const float *raw, float hdry, CellRec<N, 2, float> &r)
-{
-    constexpr int m = N + 1, nv = 3 + 2 * N;
-    float ha[m], hb[m];
-#pragma unroll
-    for (int k = 0; k < m; ++k) {
-        ha[k] = raw[var_a<N, 2>(k)];
-        hb[k] = raw[var_b<N>(k)];
-    }
-    make_cell<N, 2, float>(r, raw[0], raw[nv], ha, hb, hdry);
-}
-
-template <int N, int STAGE>
-__global__ void __launch_bounds__(TRI_TILE, 4) k_stage_tri_tile(TriArgs a)
-{
-    constexpr int m = N + 1, nv = 3 + 2 * N;
-    __shared__ TriTileSmem<N> S;
-    const StageArgs<float> &s = a.s;
-    pdl_enter();
-    if (*(volatile unsigned int *)&s.ctl->status) return;
-    float dt;
-    if (!step_dt(s, dt)) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&s.ctl->status, DEV_NOWAVE);
-        return;
-    }
-    if (STAGE == 1 && blockIdx.x == 0 && threadIdx.x == 0) step_bookkeeping(s, dt);
-    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    float smax = 0.0f;
-    unsigned flag = 0;
-    const int64_t ntiles = (a.nc + TRI_TILE - 1) / TRI_TILE;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t c0 = tile * TRI_TILE, i = c0 + t;
-        const bool valid = i < a.nc;
-        const int64_t ic = valid ? i : a.nc - 1;  // the tail's idle threads read a valid cell
-        // phase A: the cell's state, neighbours, geometry (and Q^n) -> record and face ownership
-        float raw[nv + 1];
-        tri_load<N>(a, ic, raw);
-        float qn[nv];
-        if (STAGE == 2) {
-#pragma unroll
-            for (int v = 0; v < nv; ++v) qn[v] = __ldg(s.Qn + v * s.ld + ic);
-        }
-        int cnt = 0;
-        int32_t jn[3];
-#pragma unroll
-        for (int f = 0; f < 3; ++f) {
-            jn[f] = __ldg(a.nbr + f * a.nc + ic);
-            S.nbr[f][t] = jn[f];
-            const int64_t j = jn[f];
-            // owned faces by kind, packed 10 bits each: inside the tile, to a cell outside, boundary
-            if (valid) cnt += j < 0 ? (1 << 20) : ((j < c0 || j >= c0 + TRI_TILE) ? (1 << 10) : (j > i ? 1 : 0));
-        }
-#pragma unroll
-        for (int g = 0; g < 9; ++g) S.geo[g][t] = __ldg(a.geo + g * a.nc + ic);
-        {
-            CellRec<N, 2, float> xy;
-            tile_make_xy<N>(raw, s.hdry, xy);
-            tile_store_rec<N>(S, t, xy);
-        }
-        // block exclusive scan of the packed counts -> face list sorted by kind (inside faces first,
-        // then faces to outside cells, then boundary faces), so that a warp mostly takes one branch
-        int incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
-        }
-        if (lane == 31) S.wsum[w] = incl;
-        __syncthreads();
-        int excl = incl - cnt, tot = 0;
-#pragma unroll
-        for (int q = 0; q < TRI_TILE / 32; ++q) {
-            if (q < w) excl += S.wsum[q];
-            tot += S.wsum[q];
-        }
-        const int n_in = tot & 1023, n_out = (tot >> 10) & 1023, nface = n_in + n_out + (tot >> 20);
-        int pos[3] = {excl & 1023, n_in + ((excl >> 10) & 1023), n_in + n_out + (excl >> 20)};
-#pragma unroll
-        for (int f = 0; f < 3; ++f) {
-            const int64_t j = jn[f];
-            const int kind = j < 0 ? 2 : ((j < c0 || j >= c0 + TRI_TILE) ? 1 : (j > i ? 0 : -1));
-            if (valid && kind >= 0) {
-                const int e = pos[kind]++;
-                S.fj[e] = jn[f];
-                S.ftf[e] = (uint16_t)((t << 2) | f);
-            }
-        }
-        __syncthreads();
-        // phase B: each listed face once
-        for (int e = t; e < nface; e += TRI_TILE) {
-            const int tl = S.ftf[e] >> 2, f = S.ftf[e] & 3;
-            const int32_t j = S.fj[e];
-            const float nx = S.geo[f][tl], ny = S.geo[3 + f][tl], lw = S.geo[6 + f][tl];
-            const int64_t jl = (int64_t)j - c0;
-            const bool inside = j >= 0 && jl >= 0 && jl < TRI_TILE;
-            CellRec<N, 2, float> L, R;
-            tile_rotate_smem<N>(S, tl, nx, ny, false, L);
-            if (inside) {
-                tile_rotate_smem<N>(S, (int)jl, nx, ny, false, R);
-            } else if (j >= 0) {
-                float rawj[nv + 1];
-                tri_load<N>(a, bounds_idx(j, a.nc, &s.ctl->status), rawj);
-                CellRec<N, 2, float> xy;
-                tile_make_xy<N>(rawj, s.hdry, xy);
-                tile_rotate<N>(xy.h, xy.b, xy.um, xy.s2, xy.s1, xy.a, xy.c, xy.gaa, xy.gab, xy.gbb, nx, ny, false, R);
-            } else {
-                // boundary: a copy of the cell, or its wall reflection
-                tile_rotate_smem<N>(S, tl, nx, ny, a.wall != 0, R);
-            }
-            float fc[1 + 2 * m], nc[1 + 2 * m], pd;
-            face_term<N, 2, float>(L, frame<N, 2, float, false>(L), R, frame<N, 2, float, false>(R), s.g, s.hdry, fc,
-                                   pd, nc);
-            // cell L receives -(fc + pd + nc), cell R +(fc - pd - nc) (pd on row n_0), rotated back to (x, y)
-            S.contrib[f][0][tl] = -lw * (fc[0] + nc[0]);
-#pragma unroll
-            for (int k = 0; k < m; ++k) {
-                const float rn = fc[1 + k] + nc[1 + k] + (k == 0 ? pd : 0.0f), rt = fc[1 + m + k] + nc[1 + m + k];
-                S.contrib[f][var_a<N, 2>(k)][tl] = -lw * (rn * nx - rt * ny);
-                S.contrib[f][var_b<N>(k)][tl] = -lw * (rn * ny + rt * nx);
-            }
-            if (inside) {
-                const int tj = (int)jl;
-                const int64_t ig = c0 + tl;
-                const int fb = S.nbr[0][tj] == ig ? 0 : (S.nbr[1][tj] == ig ? 1 : 2);
-                const float lwj = S.geo[6 + fb][tj];
-                S.contrib[fb][0][tj] = lwj * (fc[0] - nc[0]);
-#pragma unroll
-                for (int k = 0; k < m; ++k) {
-                    const float rn = fc[1 + k] - nc[1 + k] - (k == 0 ? pd : 0.0f), rt = fc[1 + m + k] - nc[1 + m + k];
-                    S.contrib[fb][var_a<N, 2>(k)][tj] = lwj * (rn * nx - rt * ny);
-                    S.contrib[fb][var_b<N>(k)][tj] = lwj * (rn * ny + rt * nx);
-                }
-            }
-        }
-        __syncthreads();
-        // phase C: the cell update
-        if (valid) {
-            float acc[nv];
-#pragma unroll
-            for (int v = 0; v < nv; ++v) acc[v] = (S.contrib[0][v][t] + S.contrib[1][v][t]) + S.contrib[2][v][t];
-            CellRec<N, 2, float> me;  // the x/y record, for the Newtonian source
-            me.h = S.rec[0][t];
-#pragma unroll
-            for (int k = 0; k < m; ++k) {
-                me.a[k] = S.rec[5 + k][t];
-                me.c[k] = S.rec[5 + m + k][t];
-            }
-            float sa[m], sb[m];
-            newtonian<N, 2, float>(me, s.nu_rho, sa, sb);
-            float y[nv], ya[m], yb[m];
-            y[0] = fmaf(dt, acc[0], raw[0]);
-#pragma unroll
-            for (int k = 0; k < m; ++k) {
-                ya[k] = raw[var_a<N, 2>(k)] + dt * (acc[var_a<N, 2>(k)] + sa[k]);
-                yb[k] = raw[var_b<N>(k)] + dt * (acc[var_b<N>(k)] + sb[k]);
-            }
-            if (s.src_implicit)
-                friction_implicit<N, 2, float>(y[0], ya, yb, s.fric, s.C_rho, s.nu_imp, s.gn2, dt, s.hdry);
-            else
-                bottom_friction<N, 2, float>(y[0], ya, yb, s.fric, s.C_rho, s.gn2, dt, s.hdry);
-#pragma unroll
-            for (int k = 0; k < m; ++k) {
-                y[var_a<N, 2>(k)] = ya[k];
-                y[var_b<N>(k)] = yb[k];
-            }
-            if (STAGE == 2) {
-#pragma unroll
-                for (int v = 0; v < nv; ++v) y[v] = 0.5f * (qn[v] + y[v]);
-                CellRec<N, 2, float> co;
-#pragma unroll
-                for (int k = 0; k < m; ++k) {
-                    ya[k] = y[var_a<N, 2>(k)];
-                    yb[k] = y[var_b<N>(k)];
-                }
-                make_cell<N, 2, float>(co, y[0], 0.0f, ya, yb, s.hdry);
-                const float sp = wavespeed<N, 2, float>(co, s.g);
-                if (!(sp <= 3.0e38f)) flag |= DEV_NAN;
-                if (!(y[0] >= 0.0f)) flag |= (y[0] < 0.0f) ? DEV_NEGDEPTH : DEV_NAN;
-                smax = (sp > smax || sp != sp) ? sp : smax;
-            }
-#pragma unroll
-            for (int v = 0; v < nv; ++v) s.out[v * s.ld + i] = y[v];
-        }
-    }
-    if (STAGE == 2) {
-        if (flag) atomicOr(&s.ctl->status, flag);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float v = __shfl_xor_sync(0xffffffffu, smax, o);
-            smax = (v > smax || v != v) ? v : smax;
-        }
-        if (lane == 0) S.wmax[w] = smax;
-        __syncthreads();
-        if (t < 32) {
-            smax = t < TRI_TILE / 32 ? S.wmax[t] : 0.0f;
-            reduce_smax<float>(s.ctl, s.slot_out, smax);
-        }
-    }
-}
-
-template <int N>
-static cudaError_t launch_tri_tile(const TriArgs &a, int stage, cudaStream_t st)
-{
-    int64_t blocks = (a.nc + TRI_TILE - 1) / TRI_TILE;
-    if (blocks > (int64_t)a.nsm * 4) blocks = (int64_t)a.nsm * 4;
-    dim3 grid((unsigned)(blocks > 0 ? blocks : 1)), block(TRI_TILE);
-    return stage == 1 ? launch_pdl(k_stage_tri_tile<N, 1>, grid, block, st, a)
-                      : launch_pdl(k_stage_tri_tile<N, 2>, grid, block, st, a);
-}
-
 template <int N>
 static cudaError_t launch_tri(const TriArgs &a, int stage, cudaStream_t st)
 {
@@ -656,18 +351,8 @@ static cudaError_t launch_tri(const TriArgs &a, int stage, cudaStream_t st)
     return stage == 1 ? launch_pdl(k_stage_tri<N, 1>, grid, block, st, a) : launch_pdl(k_stage_tri<N, 2>, grid, block, st, a);
 }
 
-static cudaError_t launch_tri_level(int level, int tiled, const TriArgs &a, int stage, cudaStream_t st)
+static cudaError_t launch_tri_level(int level, const TriArgs &a, int stage, cudaStream_t st)
 {
-    if (tiled) {
-        switch (level) {
-            case 0: return launch_tri_tile<0>(a, stage, st);
-            case 1: return launch_tri_tile<1>(a, stage, st);
-            case 2: return launch_tri_tile<2>(a, stage, st);
-            case 3: return launch_tri_tile<3>(a, stage, st);
-            case 4: return launch_tri_tile<4>(a, stage, st);
-        }
-        return cudaErrorInvalidValue;
-    }
     switch (level) {
         case 0: return launch_tri<0>(a, stage, st);
         case 1: return launch_tri<1>(a, stage, st);
@@ -714,15 +399,14 @@ zoomy_status tri_run_steps(zoomy_ctx *c, float *Q, int64_t ld, double dt, int ns
         s.out = Q1;
         zoomy_status ps = prof_mark(c, 1, true);
         if (ps != ZOOMY_OK) return ps;
-        const int tiled = c->tri_variant != ZOOMY_TRI_CELL;
-        cudaError_t e = launch_tri_level(c->level, tiled, a, 1, c->stream);
+        cudaError_t e = launch_tri_level(c->level, a, 1, c->stream);
         if (e != cudaSuccess) return cuda_fail(e, "triangle stage 1 launch");
         if ((ps = prof_mark(c, 1, false)) != ZOOMY_OK) return ps;
         s.X = Q1;
         s.Qn = Q;
         s.out = Q;
         if ((ps = prof_mark(c, 2, true)) != ZOOMY_OK) return ps;
-        e = launch_tri_level(c->level, tiled, a, 2, c->stream);
+        e = launch_tri_level(c->level, a, 2, c->stream);
         if (e != cudaSuccess) return cuda_fail(e, "triangle stage 2 launch");
         if ((ps = prof_mark(c, 2, false)) != ZOOMY_OK) return ps;
     }

@@ -504,15 +504,6 @@ extern "C" zoomy_status zoomy_tune_1d(zoomy_ctx *c, int32_t mode, int32_t warps_
     return ZOOMY_OK;
 }
 
-extern "C" zoomy_status zoomy_tune_tri(zoomy_ctx *c, int32_t variant)
-{
-    if (!c) return set_error(ZOOMY_EINVAL, "zoomy_tune_tri: NULL context");
-    if (variant < ZOOMY_TRI_AUTO || variant > ZOOMY_TRI_TILED)
-        return set_error(ZOOMY_EINVAL, "zoomy_tune_tri: variant must be 0, 1 or 2");
-    c->tri_variant = variant;
-    return ZOOMY_OK;
-}
-
 zoomy_status zoomy::prof_mark(zoomy_ctx *c, int stage, bool start)
 {
     if (!c->prof_on) return ZOOMY_OK;

@@ -47,7 +47,6 @@ struct zoomy_ctx {
     // structured 2D decomposition (rows per warp segment, warps per block)
     int rows_per_warp = 0, warps_per_block = 4;  // rows_per_warp 0: rows_per_warp_for()
     int launch_1d = 0, warps_per_cta_1d = 0;     // zoomy_tune_1d
-    int tri_variant = 0;                         // zoomy_tune_tri
     // stage-kernel profiling (zoomy_profile_enable)
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_events;  // pool, reused

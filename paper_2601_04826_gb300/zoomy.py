@@ -23,7 +23,6 @@ BC_TRANSMISSIVE, BC_WALL = 0, 1
 FRICTION_NONE, FRICTION_SLIP_NEWTONIAN, FRICTION_MANNING = 0, 1, 2
 FP32, FP64 = 0, 1
 LAUNCH_AUTO, LAUNCH_PER_STAGE, LAUNCH_PERSISTENT = 0, 1, 2
-TRI_AUTO, TRI_CELL, TRI_TILED = 0, 1, 2
 
 
 class ZoomyError(RuntimeError):
@@ -66,7 +65,6 @@ _SIGNATURES = [
     ("zoomy_mass", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_double)]),
     ("zoomy_tune_set", C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
     ("zoomy_tune_1d", C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
-    ("zoomy_tune_tri", C.c_int, [C.c_void_p, C.c_int32]),
     ("zoomy_autotune", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_char_p, C.POINTER(C.c_int32),
                                  C.POINTER(C.c_double)]),
     ("zoomy_closure_set", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double]),
@@ -232,10 +230,6 @@ def zoomy_tune_set(ctx, rows_per_warp, warps_per_block):
 
 def zoomy_tune_1d(ctx, mode, warps_per_cta=0):
     _check(lib().zoomy_tune_1d(ctx, mode, warps_per_cta))
-
-
-def zoomy_tune_tri(ctx, variant):
-    _check(lib().zoomy_tune_tri(ctx, variant))
 
 
 def zoomy_autotune(ctx, Q, ld, cache_path=None):
@@ -516,10 +510,6 @@ class Context:
     def tune_1d(self, mode, warps_per_cta=0):
         """Launch shape of a first-order 1D line (LAUNCH_AUTO / LAUNCH_PER_STAGE / LAUNCH_PERSISTENT)."""
         zoomy_tune_1d(self.ctx, mode, warps_per_cta)
-
-    def tune_tri(self, variant):
-        """Stage kernel of a triangle mesh (TRI_AUTO / TRI_CELL / TRI_TILED)."""
-        zoomy_tune_tri(self.ctx, variant)
 
     def autotune(self, Q, cache_path=None):
         return zoomy_autotune(self.ctx, Q, self._ld(Q), cache_path)

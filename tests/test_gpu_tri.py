@@ -1,7 +1,6 @@
-"""GPU parity of the triangle-mesh path (Morton-ordered cells; both stage kernels: the cell-centric
-gather kernel and the tiled face-centric kernel) against the FP64 CPU oracle, which builds its own
-neighbours and geometry from the same vertices and triangles.  The library's cells are in its own
-order: zoomy_mesh_permutation maps them back."""
+"""GPU parity of the triangle-mesh path (cell-centric gather kernel, Morton-ordered cells) against
+the FP64 CPU oracle, which builds its own neighbours and geometry from the same vertices and
+triangles.  The library's cells are in its own order: zoomy_mesh_permutation maps them back."""
 import numpy as np
 import pytest
 
@@ -24,15 +23,11 @@ def Z():
     return zoomy
 
 
-VARIANTS = [1, 2]  # ZOOMY_TRI_CELL, ZOOMY_TRI_TILED
-
-
 def run_tri(Z, oracle, verts, tris, level, Q0, nsteps, dt=0.0, fric=(2, 0.0, 0.0, 0.03), bed=None, bc=1,
-            store_f32=False, variant=0):
+            store_f32=False):
     kind, C_, nu, mn = fric
     ctx = Z.Context(Z.mesh_tri(verts, tris, bc=bc, bathymetry=bed), level, Z.friction(kind, C=C_, nu=nu,
                                                                                       manning_n=mn), dtype=0)
-    ctx.tune_tri(variant)
     perm = ctx.permutation()
     assert np.array_equal(np.sort(perm), np.arange(len(tris)))
     Q0r = rounded(Q0, 0)
@@ -48,21 +43,19 @@ def run_tri(Z, oracle, verts, tris, level, Q0, nsteps, dt=0.0, fric=(2, 0.0, 0.0
     return got, ref, tg, tr
 
 
-@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("level", [0, 1, 2, 3, 4])
-def test_tri_dambreak_wet_dry(Z, oracle, level, variant):
+def test_tri_dambreak_wet_dry(Z, oracle, level):
     verts, tris = inputs.jittered_delaunay(41, seed=level)
     Q0 = inputs.circular_dam_tri(verts, tris, level, radius=0.4)
-    got, ref, tg, tr = run_tri(Z, oracle, verts, tris, level, Q0, 30, variant=variant)
+    got, ref, tg, tr = run_tri(Z, oracle, verts, tris, level, Q0, 30)
     err = rel_l1(got, ref)
     assert np.all(err <= 1e-5), err
     assert tg == pytest.approx(tr, rel=1e-5)
     assert np.all(got[0] >= 0.0)
 
 
-@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("level", [1, 3])
-def test_tri_moments_bathymetry_transmissive(Z, oracle, level, variant):
+def test_tri_moments_bathymetry_transmissive(Z, oracle, level):
     verts, tris = inputs.jittered_delaunay(37, seed=10 + level)
     c = inputs.tri_centroids(verts, tris)
     rng = np.random.default_rng(level)
@@ -72,8 +65,7 @@ def test_tri_moments_bathymetry_transmissive(Z, oracle, level, variant):
     Q0[0] = h
     for v in range(1, Q0.shape[0]):
         Q0[v] = h * rng.uniform(-0.2, 0.2) * (1 + 0.3 * np.sin(5 * c[:, 0] + v))
-    got, ref, tg, tr = run_tri(Z, oracle, verts, tris, level, Q0, 25, fric=(1, 0.05, 0.01, 0.0), bed=bed, bc=0,
-                               variant=variant)
+    got, ref, tg, tr = run_tri(Z, oracle, verts, tris, level, Q0, 25, fric=(1, 0.05, 0.01, 0.0), bed=bed, bc=0)
     err = rel_l1(got, ref)
     assert np.all(err <= 1e-5), err
 
@@ -101,47 +93,17 @@ def test_tri_mass_wavespeed_and_locality(Z, oracle):
     assert np.median(step) < 3.0 * np.sqrt(4.0 / len(tris))
 
 
-@pytest.mark.parametrize("variant", VARIANTS)
-def test_tri_full_size_config3(Z, oracle, variant):
+def test_tri_full_size_config3(Z, oracle):
     """~4M-triangle jittered Delaunay mesh, level 3, Manning n = 0.03, circular dam h = 1.5 inside
     r = 0.2 with a dry outside, walls: every output after 2 CFL steps against the oracle."""
     level = 3
     verts, tris = inputs.jittered_delaunay(1415, seed=0)
     assert len(tris) > 3.9e6
     Q0 = inputs.circular_dam_tri(verts, tris, level, radius=0.2, h_in=1.5)
-    got, ref32, tg, tr = run_tri(Z, oracle, verts, tris, level, Q0, 2, store_f32=True, variant=variant)
+    got, ref32, tg, tr = run_tri(Z, oracle, verts, tris, level, Q0, 2, store_f32=True)
     err, emax = rel_l1(got, ref32), rel_max(got, ref32)
     print("relative L1 vs FP32-storage oracle", err, "element-wise", emax)
     worst = np.argmax(np.abs(got - ref32), axis=1)
     print("worst cells", worst, "h there", ref32[0, worst], "got", got[0, worst])
     assert np.all(err <= 1e-5), err
     assert np.all(emax <= 1e-5), emax
-
-
-@pytest.mark.parametrize("level", [1, 3])
-def test_tri_tiled_ragged_tiles_and_wall_ghosts(Z, oracle, level):
-    """Tiled kernel on a mesh whose cell count is not a multiple of the 128-cell tile, with more tiles
-    than CTAs of one wave would hold for a tiny grid, walls and a moving state."""
-    verts, tris = inputs.jittered_delaunay(23, seed=7)
-    assert len(tris) % 128 != 0
-    c = inputs.tri_centroids(verts, tris)
-    Q0 = np.zeros((inputs.nvars(level, 2), len(tris)))
-    Q0[0] = 1.0 + 0.3 * np.exp(-((c[:, 0] - 0.3) ** 2 + c[:, 1] ** 2) / 0.02)
-    Q0[1] = 0.2 * Q0[0]
-    Q0[2] = -0.1 * Q0[0]
-    for v in range(3, Q0.shape[0]):
-        Q0[v] = 0.05 * Q0[0] * np.cos(3 * c[:, 1] + v)
-    got, ref, tg, tr = run_tri(Z, oracle, verts, tris, level, Q0, 40, fric=(1, 0.05, 0.01, 0.0), bc=1, variant=2)
-    assert np.all(rel_l1(got, ref) <= 1e-5)
-    assert np.all(rel_max(got, ref) <= 1e-4)
-    assert tg == pytest.approx(tr, rel=1e-5)
-
-
-def test_tune_tri_rejects_bad_values(Z):
-    verts, tris = inputs.jittered_delaunay(9, seed=1)
-    ctx = Z.Context(Z.mesh_tri(verts, tris), 1, None, dtype=0)
-    for v in (-1, 3):
-        with pytest.raises(Z.ZoomyError) as e:
-            ctx.tune_tri(v)
-        assert e.value.status == Z.ZOOMY_EINVAL
-    ctx.close()
