@@ -246,7 +246,7 @@ def run_ours(args, rank, world, local_rank):
     avg = avg2 if dom == 2 else avg1
     achieved = BYTES_STAGE[dom] * nc / (avg * 1e-3) / 1e9
     traffic = ncu_traffic() if dom == 2 and args.order == 1 else None
-    kname = f"k_stage_2d_f32<2,{dom}>" if args.order == 1 else f"k_stage_order2<2,2,float,{dom}>"
+    kname = f"k_stage_2d_f32<2,{dom}>" if args.order == 1 else f"k_stage_order2_march<2,float,{dom}>"
     value = job_throughput(nc, args.steps, ms * 1e-3, world)
     step_bytes = (BYTES_STAGE[1] + BYTES_STAGE[2]) * nc
     line = {

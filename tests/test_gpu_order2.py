@@ -56,6 +56,25 @@ def test_structured_2d(Z, oracle, dtype, level):
     assert tg == pytest.approx(tr, rel=1e-12 if dtype == 1 else 1e-5)
 
 
+@pytest.mark.parametrize("dtype,level,nx,ny,bc", [(0, 0, 1, 37, (0, 1, 1, 0)), (1, 4, 29, 9, (1, 1, 0, 0)),
+                                                   (0, 4, 85, 17, (0, 0, 1, 1)), (1, 1, 30, 1, (1, 0, 1, 0)),
+                                                   (0, 2, 56, 70, (1, 1, 1, 1)), (1, 3, 3, 2, (0, 1, 0, 1))])
+def test_structured_2d_shapes(Z, oracle, dtype, level, nx, ny, bc):
+    """Strip and segment edges of the row-marching kernel: one column, one row, widths at, below and above
+    multiples of the 28-column strip, every wall / transmissive mix, levels 0 and 4, every output
+    element-wise as well."""
+    Q0 = inputs.random_moments_2d(nx, ny, level, seed=7 * level + nx, vel=0.25)
+    _, bed = inputs.gaussian_bump_2d(nx, ny, level, seed=4)
+    bedr = rounded(bed, dtype)
+    got, ref, tg, tr = run_both(Z, oracle, Z.mesh_2d(nx, ny, bc=bc, bathymetry=bedr),
+                                oracle.Mesh.rect(nx, ny, 0, 1, 0, 1, bc=bc), level, 2, Q0, 12, dtype,
+                                (1, 0.1, 0.01, 0.0), bed=bedr)
+    tol = 1e-12 if dtype == 1 else 1e-5
+    assert np.all(rel_l1(got, ref) <= tol), rel_l1(got, ref)
+    assert np.all(rel_max(got, ref) <= (1e-11 if dtype == 1 else 1e-4)), rel_max(got, ref)
+    assert tg == pytest.approx(tr, rel=1e-12 if dtype == 1 else 1e-5)
+
+
 def test_wet_dry_manning_fp32(Z, oracle):
     level, nx, ny = 2, 64, 48
     X, Y = inputs.centers_2d(nx, ny)
