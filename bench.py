@@ -695,6 +695,44 @@ def cpu_baseline(args):
                       f"over cells, {secs:.1f} s"}
 
 
+def run_side_workloads(args):
+    """The other workloads, timed after the headline in the same run (shorter: fewer steps), each summarised
+    by its metric, time per step and the roofline fraction of its dominant kernel.  A workload that fails
+    is reported with its error and does not affect the headline."""
+    import argparse as _ap
+
+    import torch
+
+    runs = [("order2_2048_level2", run_ours, dict(order=2, steps=200, warmup=5, no_cpu_baseline=True, no_e2e=True)),
+            ("dambreak1d_2000_fp64", run_dambreak1d, dict(steps=400, warmup=5)),
+            ("vam1d_2000_fp64", run_vam, dict(steps=200, warmup=5)),
+            ("lift3d_2048_level2_k16", run_lift, dict(steps=20, warmup=3)),
+            ("ensemble_512_level1", run_ensemble, dict(steps=50, warmup=3)),
+            ("triangles_4m_level3", run_tri, dict(steps=100, warmup=5, tri_side=1415, tri_variant=0)),
+            ("closure_1024_to_T2", run_closure, dict(steps=1, warmup=3))]
+    out = {}
+    for name, fn, kw in runs:
+        a = _ap.Namespace(**vars(args))
+        for k, v in kw.items():
+            setattr(a, k, v)
+        t0 = time.perf_counter()
+        try:
+            line = fn(a, 0, 1, 0) if fn is run_ours else fn(a)
+            rf = line.get("roofline") or {}
+            out[name] = {"metric": line.get("metric"), "value": line.get("value"), "unit": line.get("unit"),
+                         "ms_per_step": line.get("ms_per_step"), "kernel": rf.get("kernel"), "frac": rf.get("frac"),
+                         "clocks": line.get("clocks"), "wall_s": round(time.perf_counter() - t0, 1)}
+            for extra in ("launch_shapes_us_per_step", "variants_ms_per_step", "speedup_vs_level4", "level4",
+                          "rel_l1_vs_level4"):
+                if extra in line:
+                    out[name][extra] = line[extra]
+        except Exception as e:  # noqa: BLE001 -- reported in the line, the headline stands
+            out[name] = {"error": f"{type(e).__name__}: {str(e)[:200]}"}
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -747,6 +785,8 @@ def main():
     ap.add_argument("--closure-engine", type=int, default=0, help="closure network engine: 0 tcgen05, 1 mma.sync")
     ap.add_argument("--closure-schedule", type=int, default=1, choices=[0, 1],
                     help="closure-kernels: network on every stage input (0) or once per step (1)")
+    ap.add_argument("--no-side", action="store_true",
+                    help="grid workload: skip the shorter runs of the other workloads after the headline")
     ap.add_argument("--rows-per-warp", type=int, default=0,
                     help="fixed structured-kernel segment height instead of the autotuner (profiling runs)")
     args = ap.parse_args()
@@ -778,6 +818,8 @@ def main():
         line = run_vam(args) if rank == 0 else None
     else:
         line = run_ours(args, rank, world, local_rank)
+        if line is not None and world == 1 and args.order == 1 and not args.no_side:
+            line["side_workloads"] = run_side_workloads(args)
     if rank == 0 and line is not None:
         print(json.dumps(line), flush=True)
     if world > 1 and args.impl == "ours":
