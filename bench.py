@@ -609,13 +609,18 @@ def run_lift(args):
             "gpu_launches": args.steps, "clocks": clk.summary()}
 
 
-def vam_launches_per_step(n):
-    """Wave speed, predictor, assembly, correction, and 1 + ceil(log2 N) reduction levels (N = ceil(n / 2))."""
-    N, levels, s = (n + 1) // 2, 0, 1
+def vam_launches_per_step(n, cr=2):
+    """Wave speed, predictor, assembly, correction, the block inversion, cr cyclic-reduction levels, the
+    parallel levels of the remaining system and cr back-substitutions (N = ceil(n / 2) block rows), as the
+    library launches them."""
+    N = (n + 1) // 2
+    sr, k = 1, 0
+    while k < cr and 2 * sr < N:
+        sr, k = 2 * sr, k + 1
+    levels, s = 0, sr
     while s < N:
-        levels += 1
-        s *= 2
-    return 5 + levels
+        levels, s = levels + 1, 2 * s
+    return 5 + k + levels + k
 
 
 def run_vam(args):

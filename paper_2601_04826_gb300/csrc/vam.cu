@@ -322,16 +322,20 @@ __global__ void __launch_bounds__(128) k_vam_assemble(VamArgs a)
     }
 }
 
-// One level of the block cyclic reduction (s = 0: only Y_I = D_I^{-1} (A_I | C_I | f_I)); `last`
-// writes the solution.  A half-warp per block row; lane l holds entry (r, c) = (l / 4, l % 4).
-__global__ void __launch_bounds__(128) k_vam_pcr(VamArgs a, int64_t N, int64_t s, const double *__restrict__ Yin,
-                                                 double *__restrict__ Yout, int last)
+// One level of the block cyclic reduction over the block rows I = j * step (s = 0: only
+// Y_I = D_I^{-1} (A_I | C_I | f_I)); `last` writes the solution of those rows.  step = 1 and s = 1, 2, 4, ...:
+// parallel cyclic reduction of all rows; step = 2s: a cyclic-reduction level (the rows at odd multiples
+// of s are eliminated from the system of the rows at multiples of 2s; their Y are kept for the
+// back-substitution; Yin may be Yout since the rows read and the rows written are disjoint).  A
+// half-warp per block row; lane l holds entry (r, c) = (l / 4, l % 4).
+__global__ void __launch_bounds__(128) k_vam_pcr(VamArgs a, int64_t N, int64_t s, int64_t step, const double *Yin,
+                                                 double *Yout, int last)
 {
     pdl_enter();
     if (*(volatile unsigned int *)&a.ctl->status) return;
     __shared__ double S[PCR_ROWS][4][16];
     const int hw = threadIdx.x >> 4, l = threadIdx.x & 15, r = l >> 2, c = l & 3;
-    const int64_t I = (int64_t)blockIdx.x * PCR_ROWS + hw;
+    const int64_t I = ((int64_t)blockIdx.x * PCR_ROWS + hw) * step;
     if (I >= N) return;  // the whole half-warp
     const unsigned mask = 0xffffu << (threadIdx.x & 16);
     double *row = a.rows + I * RS;
@@ -427,8 +431,32 @@ __global__ void __launch_bounds__(128) k_vam_pcr(VamArgs a, int64_t N, int64_t s
     y[16 + l] = C;
     if (c == 0) {
         y[32 + r] = F;
-        if (last && 4 * I + r < 2 * a.nc) a.rhs[4 * I + r] = F;
+        if (last) a.rhs[4 * I + r] = F;  // (a dummy cell's unknowns are 0 and never read)
     }
+}
+
+// Back-substitution of a cyclic-reduction level: the rows I = s + 2 s j, eliminated at that level, from
+// x_I = Yf_I - YA_I x_{I-s} - YC_I x_{I+s} with their Y of that level (x_{I+s} = 0 past the last row);
+// x lives in rhs, 4 unknowns per block row.  A thread per (row, component).
+__global__ void __launch_bounds__(128) k_vam_backsub(VamArgs a, int64_t N, int64_t s, const double *Y)
+{
+    pdl_enter();
+    if (*(volatile unsigned int *)&a.ctl->status) return;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t I = s + 2 * s * (t >> 2);
+    const int r = (int)(t & 3);
+    if (I >= N) return;
+    const double *y = Y + I * YS;
+    const double *xm = a.rhs + 4 * (I - s);
+    double x = y[32 + r];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) x -= y[4 * r + c] * xm[c];
+    if (I + s < N) {
+        const double *xp = a.rhs + 4 * (I + s);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) x -= y[16 + 4 * r + c] * xp[c];
+    }
+    a.rhs[4 * I + r] = x;
 }
 
 __global__ void __launch_bounds__(128) k_vam_correct(VamArgs a)
@@ -479,6 +507,10 @@ zoomy_status vam_run_steps(zoomy_ctx *c, double *Q, int64_t ld, double dt, int n
     const unsigned grid = grid_for(c->nc), grid_asm = grid_for(11 * c->nc);
     const unsigned grid_pred = grid_for((c->nc + 30) / 31 * 32);  // a warp per 31 cells
     const unsigned grid_pcr = (unsigned)((N + PCR_ROWS - 1) / PCR_ROWS);
+    // cyclic-reduction levels before the parallel reduction (each halves the rows left): two measured
+    // fastest at 2000 cells (97.9 us per step against 102.8 with none, 100.3 / 102.4 / 104.3 with 3 / 4 / 6;
+    // the levels are latency-bound, so the work saved per level gains little against the added launches)
+    const int cr = 2;
     const cudaStream_t st = c->stream;
     for (int k = 0; k < nsteps; ++k) {
         a.slot_in = k & 1;
@@ -487,12 +519,29 @@ zoomy_status vam_run_steps(zoomy_ctx *c, double *Q, int64_t ld, double dt, int n
         a.slot_out = (k + 1) & 1;  // the predictor clears the next step's slot
         if (e == cudaSuccess) e = launch_pdl(k_vam_predict, grid_pred, threads, st, a);
         if (e == cudaSuccess) e = launch_pdl(k_vam_assemble, grid_asm, threads, st, a);
-        int cur = 0;
         const unsigned bp = 16 * PCR_ROWS;
-        if (e == cudaSuccess) e = launch_pdl(k_vam_pcr, grid_pcr, bp, st, a, N, (int64_t)0, (const double *)a.Y[1], a.Y[0], (int)(N == 1));
-        for (int64_t s = 1; s < N && e == cudaSuccess; s *= 2) {
-            e = launch_pdl(k_vam_pcr, grid_pcr, bp, st, a, N, s, (const double *)a.Y[cur], a.Y[cur ^ 1], (int)(2 * s >= N));
+        auto grid_rows = [&](int64_t step) {
+            const int64_t rows = (N + step - 1) / step;
+            return (unsigned)((rows + PCR_ROWS - 1) / PCR_ROWS);
+        };
+        if (e == cudaSuccess)
+            e = launch_pdl(k_vam_pcr, grid_pcr, bp, st, a, N, (int64_t)0, (int64_t)1, (const double *)a.Y[1], a.Y[0],
+                           (int)(N == 1));
+        // cyclic-reduction levels: the system of the rows at multiples of st, st = 2, 4, ..., 2^cr
+        int64_t sr = 1;
+        for (int q = 0; q < cr && 2 * sr < N && e == cudaSuccess; ++q, sr *= 2)
+            e = launch_pdl(k_vam_pcr, grid_rows(2 * sr), bp, st, a, N, sr, 2 * sr, (const double *)a.Y[0], a.Y[0], 0);
+        // parallel cyclic reduction of that system
+        int cur = 0;
+        for (int64_t s = sr; s < N && e == cudaSuccess; s *= 2) {
+            e = launch_pdl(k_vam_pcr, grid_rows(sr), bp, st, a, N, s, sr, (const double *)a.Y[cur], a.Y[cur ^ 1],
+                           (int)(2 * s >= N));
             cur ^= 1;
+        }
+        // back-substitution of the eliminated rows (their Y are in Y[0])
+        for (int64_t s = sr / 2; s >= 1 && e == cudaSuccess; s /= 2) {
+            const int64_t rows = (N - s + 2 * s - 1) / (2 * s);
+            e = launch_pdl(k_vam_backsub, (unsigned)((4 * rows + 127) / 128), 128u, st, a, N, s, (const double *)a.Y[0]);
         }
         if (e == cudaSuccess) e = launch_pdl(k_vam_correct, grid, threads, st, a);
         if (e != cudaSuccess) return cuda_fail(e, "VAM step launch");
