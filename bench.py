@@ -713,7 +713,7 @@ def run_side_workloads(args):
             ("vam1d_2000_fp64", run_vam, dict(steps=200, warmup=5)),
             ("lift3d_2048_level2_k16", run_lift, dict(steps=20, warmup=3)),
             ("ensemble_512_level1", run_ensemble, dict(steps=50, warmup=3)),
-            ("triangles_4m_level3", run_tri, dict(steps=100, warmup=5, tri_side=1415, tri_variant=0)),
+            ("triangles_4m_level3", run_tri, dict(steps=100, warmup=5, tri_side=1415)),
             ("closure_1024_to_T2", run_closure, dict(steps=1, warmup=3))]
     out = {}
     for name, fn, kw in runs:
