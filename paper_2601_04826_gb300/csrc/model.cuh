@@ -99,11 +99,23 @@ __device__ __forceinline__ void make_cell(CellRec<N, D, T> &r, T h, T b, const T
     r.h = h;
     r.b = b;
     const bool wet = h > hdry;
+    if constexpr (sizeof(T) == 8) {
+        // FP64: one division per cell (the FP64 path is bound by its division chains on GB300); the
+        // moments are within an ulp of h alpha_k / h
+        const T ih = wet ? T(1) / h : T(0);
 #pragma unroll
-    for (int k = 0; k < m; ++k) r.a[k] = wet ? dev_div(ha[k], h) : T(0);
-    if constexpr (D == 2) {
+        for (int k = 0; k < m; ++k) r.a[k] = ha[k] * ih;
+        if constexpr (D == 2) {
 #pragma unroll
-        for (int k = 0; k < m; ++k) r.c[k] = wet ? dev_div(hb[k], h) : T(0);
+            for (int k = 0; k < m; ++k) r.c[k] = hb[k] * ih;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < m; ++k) r.a[k] = wet ? dev_div(ha[k], h) : T(0);
+        if constexpr (D == 2) {
+#pragma unroll
+            for (int k = 0; k < m; ++k) r.c[k] = wet ? dev_div(hb[k], h) : T(0);
+        }
     }
     if constexpr (D == 2)
         r.um = dev_sqrt(r.a[0] * r.a[0] + r.c[0] * r.c[0]);
