@@ -235,11 +235,26 @@ __device__ __forceinline__ void face_term(const CellRec<N, D, T> &L, const Frame
         constexpr double sq15 = 0.38729833462074168852;  // sqrt(15)/10
         const T sn[3] = {T(0.5 - sq15), T(0.5), T(0.5 + sq15)};
         const T wq[3] = {T(5.0 / 18.0), T(8.0 / 18.0), T(5.0 / 18.0)};
+        // FP64: the three reciprocals from one division of the product of the wet depths (dry nodes
+        // count as 1 and get weight 0)
+        T hqs[3], rp = T(1);
+        if constexpr (sizeof(T) == 8) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                hqs[q] = hl + sn[q] * dh;
+                if (!(hqs[q] > hdry)) hqs[q] = T(1);
+            }
+            rp = T(1) / (hqs[0] * hqs[1] * hqs[2]);
+        }
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             const T hq = hl + sn[q] * dh;
             const bool wet = hq > hdry;
-            const T iw = wet ? dev_div(wq[q], hq) : T(0);
+            T iw;
+            if constexpr (sizeof(T) == 8)
+                iw = wet ? wq[q] * (rp * hqs[(q + 1) % 3] * hqs[(q + 2) % 3]) : T(0);
+            else
+                iw = wet ? dev_div(wq[q], hq) : T(0);
 #pragma unroll
             for (int k = 0; k < m; ++k) nbar[k] += iw * (el * FL.n[k] + sn[q] * dn[k]);
             if constexpr (D == 2) {
@@ -320,17 +335,25 @@ __device__ __forceinline__ void bottom_friction(T h, T *ya, T *yb, int fric, T C
         sa += ya[k];
         if constexpr (D == 2) sb += yb[k];
     }
-    T c;
-    if (fric == 1) {
-        c = dev_div(C_rho, h);
-    } else {
-        T ub = dev_div(sa, h), vb = dev_div(sb, h);
-        T sp = (D == 2) ? dev_sqrt(ub * ub + vb * vb) : fabs(ub);
-        // h^(4/3) = h * cbrt(h)
-        c = dev_div(gn2 * sp, h * cbrt(h));
-    }
     constexpr T sw = T(m * m);  // sum_k (2k+1)
-    const T f = dev_div(dt * c, T(1) + dt * c * sw);
+    T f;
+    if (sizeof(T) == 8 && fric == 1) {
+        // FP64 slip: f = dt c / (1 + dt c sw) with c = C/(rho h) is dt C/rho / (h + dt C/rho sw), one
+        // division instead of two (the FP64 path is bound by its division chains)
+        const T dC = dt * C_rho;
+        f = dC / (h + dC * sw);
+    } else {
+        T c;
+        if (fric == 1) {
+            c = dev_div(C_rho, h);
+        } else {
+            T ub = dev_div(sa, h), vb = dev_div(sb, h);
+            T sp = (D == 2) ? dev_sqrt(ub * ub + vb * vb) : fabs(ub);
+            // h^(4/3) = h * cbrt(h)
+            c = dev_div(gn2 * sp, h * cbrt(h));
+        }
+        f = dev_div(dt * c, T(1) + dt * c * sw);
+    }
     const T fa = f * sa, fb = f * sb;
 #pragma unroll
     for (int k = 0; k < m; ++k) {
