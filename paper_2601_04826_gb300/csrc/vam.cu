@@ -104,9 +104,9 @@ __device__ __forceinline__ void vflux(const double *q, double rh, double bx, dou
     const double h = q[0], u0 = q[1] * rh, u1 = q[2] * rh, w0 = q[3] * rh, w1 = q[4] * rh;
     const double w2 = -(w0 + w1) + (u0 + u1) * bx;
     F[0] = h * u0;
-    F[1] = h * u0 * u0 + h * u1 * u1 / 3.0 + 0.5 * g * h * h;
+    F[1] = h * u0 * u0 + h * u1 * u1 * (1.0 / 3.0) + 0.5 * g * h * h;
     F[2] = 2.0 * h * u0 * u1;
-    F[3] = h * u0 * w0 + h * u1 * w1 / 3.0;
+    F[3] = h * u0 * w0 + h * u1 * w1 * (1.0 / 3.0);
     F[4] = h * u0 * w1 + u1 * (h * w0 + 0.4 * h * w2);
 }
 
@@ -134,13 +134,22 @@ __device__ __forceinline__ void vface(const double *qL, const double *qR, double
     const double bxf = 0.5 * (bxL + bxR);
     const double sq[3] = {0.5 - 0.38729833462074168852, 0.5, 0.5 + 0.38729833462074168852};
     const double wq[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+    // 1/h at the three nodes from one division of the product of the wet depths (dry: 1, weight 0);
+    // FP64 divisions are long dependent chains on GB300, and constant divisors become products
+    double hq[3];
+    for (int k = 0; k < 3; ++k) {
+        hq[k] = Ls[0] + sq[k] * dq[0];
+        if (!(hq[k] > 0.0)) hq[k] = 1.0;
+    }
+    const double rp = 1.0 / (hq[0] * hq[1] * hq[2]);
     for (int k = 0; k < 3; ++k) {
         double p[5];
         for (int v = 0; v < 5; ++v) p[v] = Ls[v] + sq[k] * dq[v];
-        const double rh = vrh(p[0]), u0 = p[1] * rh, u1 = p[2] * rh, w0 = p[3] * rh, w1 = p[4] * rh;
+        const double rh = p[0] > 0.0 ? rp * hq[(k + 1) % 3] * hq[(k + 2) % 3] : 0.0;
+        const double u0 = p[1] * rh, u1 = p[2] * rh, w0 = p[3] * rh, w1 = p[4] * rh;
         const double w2 = -(w0 + w1) + (u0 + u1) * bxf;
         bt[2] += wq[k] * (-u0) * dq[2];
-        bt[4] += wq[k] * (w2 / 5.0 - w0) * dq[2];
+        bt[4] += wq[k] * (w2 * 0.2 - w0) * dq[2];
     }
     const double sL = vspeed(Ls, rhL, g), sR = vspeed(Rs, rhR, g), sf = sL > sR ? sL : sR;
     for (int v = 0; v < 5; ++v) {
@@ -265,9 +274,9 @@ __device__ __forceinline__ void vresidual(const VamArgs &a, const Probe &pr, int
     const double h = qc[0], rh = 1.0 / h, u0 = qc[1] * rh, u1 = qc[2] * rh, w0 = qc[3] * rh, w1 = qc[4] * rh;
     const double bx = vbx_cell(a, i);
     const double dh = (qr[0] - ql[0]) * i2dx;
-    const double du0 = (qr[1] / qr[0] - ql[1] / ql[0]) * i2dx;
+    const double du0 = (qr[1] * ql[0] - ql[1] * qr[0]) / (qr[0] * ql[0]) * i2dx;
     const double dhu1 = (qr[2] - ql[2]) * i2dx;
-    R[0] = h * du0 + dhu1 / 3.0 + u1 * dh / 3.0 + 2.0 * (w0 - u0 * bx);
+    R[0] = h * du0 + (dhu1 + u1 * dh) * (1.0 / 3.0) + 2.0 * (w0 - u0 * bx);
     R[1] = h * du0 + u1 * dh + 2.0 * (u1 * bx - w1);
 }
 
