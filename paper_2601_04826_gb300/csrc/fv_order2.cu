@@ -63,10 +63,20 @@ __device__ __forceinline__ void prim(const T *q, T hdry, T *w)
     const bool wet = h > hdry;
     w[0] = h;
     w[1] = h + q[nv];
+    if constexpr (sizeof(T) == 8) {
+        // FP64: one division per cell (the FP64 path is bound by its division chains)
+        const T rh = wet ? T(1) / h : T(0);
 #pragma unroll
-    for (int k = 0; k < m; ++k) {
-        w[2 + k] = wet ? q[var_a<N, D>(k)] / h : T(0);
-        if constexpr (D == 2) w[2 + m + k] = wet ? q[var_b<N>(k)] / h : T(0);
+        for (int k = 0; k < m; ++k) {
+            w[2 + k] = q[var_a<N, D>(k)] * rh;
+            if constexpr (D == 2) w[2 + m + k] = q[var_b<N>(k)] * rh;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < m; ++k) {
+            w[2 + k] = wet ? q[var_a<N, D>(k)] / h : T(0);
+            if constexpr (D == 2) w[2 + m + k] = wet ? q[var_b<N>(k)] / h : T(0);
+        }
     }
 }
 
@@ -524,6 +534,7 @@ __global__ void __launch_bounds__(32, O2_MIN_CTAS<N, T>) k_stage_order2_march(St
             const T *x = xf;
             CellRec<N, 2, T> me;  // the Newtonian source needs h and the velocity moments (P2 = row M - 1)
             me.h = x[0];
+            me.ih = x[0] > a.hdry ? T(1) / x[0] : T(0);
 #pragma unroll
             for (int k = 0; k < m; ++k) {
                 me.a[k] = P2.w[2 + k];

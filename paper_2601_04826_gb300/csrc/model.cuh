@@ -86,6 +86,7 @@ struct CellRec {
     T a[m];      // alpha_k (x moments), zero if dry
     T c[mt];     // beta_k (y moments), zero if dry
     T um, s2, s1;  // |mean velocity|, sum_{k>=1} |a_k|^2, sum_{k>=2} |a_k|
+    T ih;          // 1/h if wet, else 0 (FP64 records; the Newtonian source reuses it)
     T gaa[m];    // sum_ij alpha_i alpha_j A_ijk / M_k
     T gab[mt];   // sum_ij alpha_i beta_j A_ijk / M_k
     T gbb[mt];   // sum_ij beta_i beta_j A_ijk / M_k
@@ -103,6 +104,7 @@ __device__ __forceinline__ void make_cell(CellRec<N, D, T> &r, T h, T b, const T
         // FP64: one division per cell (the FP64 path is bound by its division chains on GB300); the
         // moments are within an ulp of h alpha_k / h
         const T ih = wet ? T(1) / h : T(0);
+        r.ih = ih;
 #pragma unroll
         for (int k = 0; k < m; ++k) r.a[k] = ha[k] * ih;
         if constexpr (D == 2) {
@@ -110,6 +112,7 @@ __device__ __forceinline__ void make_cell(CellRec<N, D, T> &r, T h, T b, const T
             for (int k = 0; k < m; ++k) r.c[k] = hb[k] * ih;
         }
     } else {
+        r.ih = T(0);  // not used in FP32
 #pragma unroll
         for (int k = 0; k < m; ++k) r.a[k] = wet ? dev_div(ha[k], h) : T(0);
         if constexpr (D == 2) {
@@ -293,7 +296,12 @@ template <int N, int D, typename T>
 __device__ __forceinline__ void newtonian(const CellRec<N, D, T> &r, T nu_rho, T *sa, T *sb)
 {
     constexpr int m = N + 1;
-    const T f = r.h > T(0) ? dev_div(nu_rho, r.h) : T(0);
+    // FP64: the record's 1/h (0 where dry, where the velocity moments are 0 too), no second division
+    T f;
+    if constexpr (sizeof(T) == 8)
+        f = nu_rho * r.ih;
+    else
+        f = r.h > T(0) ? dev_div(nu_rho, r.h) : T(0);
     static_for<0, m>([&](auto kk) {
         constexpr int k = decltype(kk)::value;
         T xa = 0;

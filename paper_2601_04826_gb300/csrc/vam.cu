@@ -119,7 +119,10 @@ __device__ __forceinline__ void vface(const double *qL, const double *qR, double
 {
     const double bf = fmax(bL, bR);
     const double hLs = fmax(0.0, qL[0] + bL - bf), hRs = fmax(0.0, qR[0] + bR - bf);
-    const double fL = qL[0] > 0.0 ? hLs / qL[0] : 0.0, fR = qR[0] > 0.0 ? hRs / qR[0] : 0.0;
+    // f = h* / h and 1/h* of each side from one division: 1/(h h*) (both zero where h* = 0)
+    const bool wL = qL[0] > 0.0 && hLs > 0.0, wR = qR[0] > 0.0 && hRs > 0.0;
+    const double rL = wL ? 1.0 / (qL[0] * hLs) : 0.0, rR = wR ? 1.0 / (qR[0] * hRs) : 0.0;
+    const double fL = hLs * hLs * rL, fR = hRs * hRs * rR;
     double Ls[5], Rs[5], FL[5], FR[5], dq[5], bt[5] = {0, 0, 0, 0, 0};
     Ls[0] = hLs;
     Rs[0] = hRs;
@@ -127,7 +130,7 @@ __device__ __forceinline__ void vface(const double *qL, const double *qR, double
         Ls[v] = qL[v] * fL;
         Rs[v] = qR[v] * fR;
     }
-    const double rhL = vrh(hLs), rhR = vrh(hRs);
+    const double rhL = qL[0] * rL, rhR = qR[0] * rR;
     vflux(Ls, rhL, bxL, g, FL);
     vflux(Rs, rhR, bxR, g, FR);
     for (int v = 0; v < 5; ++v) dq[v] = Rs[v] - Ls[v];
